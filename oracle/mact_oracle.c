@@ -1,0 +1,557 @@
+/*
+ * mact_oracle.c -- plain FP64 CPU oracle for the MACT per-pixel transforms.
+ *
+ * TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline / reference legs may load this library.  It shares no code,
+ * header or table with the CUDA library; it is the slow, obviously correct
+ * statement of what the paper computes, against which the kernels are checked.
+ *
+ * Everything is double precision, one pixel at a time, in the order the paper
+ * writes the formulas.  Polynomials are evaluated as the plain sum
+ * a0 + a1 x + a2 x^2 + ... (no Horner restructuring, no fusion).  The only
+ * concession to speed is an OpenMP "parallel for" over independent pixels
+ * (and a reduction for the error statistics), which changes no per-pixel
+ * arithmetic.
+ *
+ * Readings of the paper taken here (each one is pinned by a test):
+ *  - CIELAB, HSI and SCT take 8-bit codes.  CIELAB linearises k' = code/255
+ *    with the BT.709 inverse gamma (Eq. equ_rgb_lin); HSI and SCT work on the
+ *    gamma-encoded codes directly.
+ *  - f(t) uses the approximant only for t > 0.008856 (Eq. equ_xyz_lab); the
+ *    linear segment 7.787 t + 16/116 is kept exactly.  No clamp of t to 1.
+ *  - HSI hue: Kender's case chain (Eq. equ_rgb_kender) evaluated in the
+ *    printed order with strict comparisons; hue 0 when max-min (chroma) is 0
+ *    (the "undefined" case); S = 0 for black.
+ *  - SCT: x = B/L; arcsin form when x >= 0.5 (Eq. equ_arccos_stable /
+ *    equ_arccos_cheap), arccos polynomial otherwise; angle B uses f(G/R)
+ *    when G < R and g(R/G) otherwise (Eq. arctan_split); R=0,G>0 gives pi/2;
+ *    R=G=0 gives 0; black gives L = A = B = 0.
+ *  - LUT nodes sit at k' = i/(N-1) on each axis (R outermost); the cell of a
+ *    code v is idx = v(N-1) div 255 with remainder rem = v(N-1) mod 255,
+ *    except v = 255 which uses idx = N-2, rem = 255.  Simplex choice compares
+ *    the integer remainders.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_API __attribute__((visibility("default")))
+
+/* Source RGB definition: BT.709 inverse gamma parameters, the RGB->XYZ
+ * matrix (row-major) and the reference white (Eq. equ_rgb_lin, equ_rgb_xyz
+ * and the D65 white point of Section "Color Space Description"). */
+typedef struct {
+    double threshold, slope, offset, exponent;
+    double m[9];
+    double white[3];
+} orc_rgbdef;
+
+static const double ORC_PI = 3.14159265358979323846264338327950288;
+
+/* ---------------------------------------------------------------- helpers */
+
+/* p(x) = a[0] + a[1] x + ... + a[n] x^n, written as the plain sum. */
+static double orc_poly(const double *a, int n, double x)
+{
+    double s = 0.0, xp = 1.0;
+    for (int i = 0; i <= n; ++i) {
+        s += a[i] * xp;
+        xp *= x;
+    }
+    return s;
+}
+
+static void orc_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+ORC_API int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ CIELAB */
+
+/* Eq. equ_rgb_lin: nonlinear k' in [0,1] -> linear k (BT.709). */
+ORC_API double orc_gamma_inverse(const orc_rgbdef *d, double kp)
+{
+    if (kp < d->threshold) return kp / d->slope;
+    return pow((kp + d->offset) / (1.0 + d->offset), d->exponent);
+}
+
+/* Eq. equ_rgb_xyz followed by the division by the reference white:
+ * t = (X/X0, Y/Y0, Z/Z0) for 8-bit codes (r, g, b). */
+ORC_API void orc_rgb_to_t(const orc_rgbdef *d, double r, double g, double b, double t[3])
+{
+    double k[3];
+    k[0] = orc_gamma_inverse(d, r / 255.0);
+    k[1] = orc_gamma_inverse(d, g / 255.0);
+    k[2] = orc_gamma_inverse(d, b / 255.0);
+    for (int c = 0; c < 3; ++c) {
+        double xyz = d->m[3 * c + 0] * k[0] + d->m[3 * c + 1] * k[1] + d->m[3 * c + 2] * k[2];
+        t[c] = xyz / d->white[c];
+    }
+}
+
+/* Eq. equ_xyz_lab, exact f(t). */
+static double orc_f_exact(double t)
+{
+    if (t > 0.008856) return cbrt(t);
+    return 7.787 * t + 16.0 / 116.0;
+}
+
+/* f(t) with the cube root replaced by p_n(t)/q_m(t) (Tables tab_cbrt_rat,
+ * tab_cbrt_poly; m < 0 means a polynomial, i.e. q = 1). */
+static double orc_f_approx(double t, const double *p, int n, const double *q, int m)
+{
+    if (t > 0.008856) {
+        double num = orc_poly(p, n, t);
+        double den = (m >= 0) ? orc_poly(q, m, t) : 1.0;
+        return num / den;
+    }
+    return 7.787 * t + 16.0 / 116.0;
+}
+
+/* L*, a*, b* from f values (Eq. equ_xyz_lab). */
+static void orc_lab_from_f(double fx, double fy, double fz, double lab[3])
+{
+    lab[0] = 116.0 * fy - 16.0;
+    lab[1] = 500.0 * (fx - fy);
+    lab[2] = 200.0 * (fy - fz);
+}
+
+/* One pixel of RGB -> CIELAB.  mode 0: exact; mode 1: MACT approximant. */
+ORC_API void orc_cielab_pixel(const orc_rgbdef *d, int mode,
+                              const double *p, int n, const double *q, int m,
+                              double r, double g, double b, double lab[3])
+{
+    double t[3], f[3];
+    orc_rgb_to_t(d, r, g, b, t);
+    for (int c = 0; c < 3; ++c)
+        f[c] = mode ? orc_f_approx(t[c], p, n, q, m) : orc_f_exact(t[c]);
+    orc_lab_from_f(f[0], f[1], f[2], lab);
+}
+
+ORC_API void orc_cielab(const orc_rgbdef *d, int mode,
+                        const double *p, int n, const double *q, int m,
+                        const uint8_t *rgb, int64_t npix,
+                        double *L, double *A, double *B, int nthreads)
+{
+    orc_set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < npix; ++i) {
+        double lab[3];
+        orc_cielab_pixel(d, mode, p, n, q, m, rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2], lab);
+        L[i] = lab[0];
+        A[i] = lab[1];
+        B[i] = lab[2];
+    }
+}
+
+/* Eq. equ_cielab_dist. */
+ORC_API double orc_delta_e(const double x[3], const double y[3])
+{
+    double dl = x[0] - y[0], da = x[1] - y[1], db = x[2] - y[2];
+    return sqrt(dl * dl + da * da + db * db);
+}
+
+/* --------------------------------------------------------------------- HSI */
+
+/* arctan(sqrt(3) x) -- exact, or sgn(x) P_n(|x|) (Table tab_arctan and the
+ * odd-symmetry identity of Section "Approximation of the Inverse Tangent
+ * Function"). */
+static double orc_atan_sqrt3(double x, const double *c, int n)
+{
+    if (!c) return atan(sqrt(3.0) * x);
+    if (x < 0.0) return -orc_poly(c, n, -x);
+    return orc_poly(c, n, x);
+}
+
+/* Eq. equ_rgb_kender hue (radians) on codes r, g, b; c == NULL is exact. */
+static double orc_hue_kender(double r, double g, double b, const double *c, int n)
+{
+    if (r > b && g > b) return ORC_PI / 3.0 + orc_atan_sqrt3((g - r) / (g - b + r - b), c, n);
+    if (g > r) return ORC_PI + orc_atan_sqrt3((b - g) / (b - r + g - r), c, n);
+    if (b > g) return 5.0 * ORC_PI / 3.0 + orc_atan_sqrt3((r - b) / (r - g + b - g), c, n);
+    if (r > b) return 0.0;
+    return 0.0; /* undefined (gray): convention H = 0 */
+}
+
+/* Eq. equ_rgb_hsi hue via arccos (the original form), for cross-checking. */
+static double orc_hue_arccos(double r, double g, double b)
+{
+    double den = sqrt((r - g) * (r - g) + (r - b) * (g - b));
+    if (den == 0.0) return 0.0;
+    double c = 0.5 * (r - g + r - b) / den;
+    if (c > 1.0) c = 1.0;
+    if (c < -1.0) c = -1.0;
+    double h = acos(c);
+    if (b > g) h = 2.0 * ORC_PI - h;
+    return h;
+}
+
+/* One pixel of RGB -> HSI.  mode 0: Kender exact, 1: Kender with P_n,
+ * 2: arccos form.  H in radians, S and I in [0,1] with R = R'/255. */
+ORC_API void orc_hsi_pixel(int mode, const double *c, int n,
+                           double r, double g, double b, double hsi[3])
+{
+    double sum = r + g + b;
+    double mn = r < g ? (r < b ? r : b) : (g < b ? g : b);
+    if (mode == 2)
+        hsi[0] = orc_hue_arccos(r, g, b);
+    else
+        hsi[0] = orc_hue_kender(r, g, b, mode == 1 ? c : NULL, n);
+    hsi[1] = sum > 0.0 ? 1.0 - 3.0 * mn / sum : 0.0;
+    hsi[2] = (sum / 255.0) / 3.0;
+}
+
+ORC_API void orc_hsi(int mode, const double *c, int n,
+                     const uint8_t *rgb, int64_t npix,
+                     double *H, double *S, double *I, int nthreads)
+{
+    orc_set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < npix; ++i) {
+        double hsi[3];
+        orc_hsi_pixel(mode, c, n, rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2], hsi);
+        H[i] = hsi[0];
+        S[i] = hsi[1];
+        I[i] = hsi[2];
+    }
+}
+
+/* Eq. equ_hsi_dist. */
+ORC_API double orc_d_hsi(const double x[3], const double y[3])
+{
+    double dh = fabs(x[0] - y[0]);
+    double th = dh <= ORC_PI ? dh : 2.0 * ORC_PI - dh;
+    double di = x[2] - y[2];
+    double v = x[1] * x[1] + y[1] * y[1] - 2.0 * x[1] * y[1] * cos(th) + di * di;
+    return sqrt(v > 0.0 ? v : 0.0);
+}
+
+/* --------------------------------------------------------------------- SCT */
+
+typedef struct {
+    const double *p; int n;   /* Table tab_arcsin: 2 arcsin(y/sqrt2), y = sqrt(1-x) */
+    const double *q; int m;   /* Table tab_arccos: arccos(x) on [0, 0.5]           */
+    const double *f; int rf;  /* Table tab_f: arctan(x) on [0, 254/255]            */
+    const double *g; int rg;  /* Table tab_g: pi/2 - arctan(w) on [1/255, 1]       */
+} orc_sct_coeffs;
+
+/* One pixel of RGB -> SCT (Eq. equ_rgb_sct with Eq. equ_sct_b).
+ * co == NULL: exact.  Output (L, angle A, angle B), L in code units. */
+ORC_API void orc_sct_pixel(const orc_sct_coeffs *co, double r, double g, double b, double out[3])
+{
+    double L = sqrt(r * r + g * g + b * b);
+    double A, B;
+    if (L == 0.0) {
+        out[0] = 0.0; out[1] = 0.0; out[2] = 0.0;
+        return;
+    }
+    double x = b / L;
+    if (!co) {
+        A = acos(x);
+    } else if (x >= 0.5) {
+        double y = sqrt(1.0 - x);                 /* Eq. equ_arccos_cheap */
+        A = orc_poly(co->p, co->n, y);
+    } else {
+        A = orc_poly(co->q, co->m, x);
+    }
+    if (r == 0.0 && g == 0.0) {
+        B = 0.0;                                  /* undefined: convention 0 */
+    } else if (!co) {
+        B = atan2(g, r);
+    } else if (r == 0.0) {
+        B = ORC_PI / 2.0;                         /* R = 0, G > 0 */
+    } else if (g < r) {
+        B = orc_poly(co->f, co->rf, g / r);       /* f(G/R) */
+    } else {
+        B = orc_poly(co->g, co->rg, r / g);       /* g: pi/2 - arctan(R/G) */
+    }
+    out[0] = L;
+    out[1] = A;
+    out[2] = B;
+}
+
+ORC_API void orc_sct(const orc_sct_coeffs *co, const uint8_t *rgb, int64_t npix,
+                     double *Lo, double *Ao, double *Bo, int nthreads)
+{
+    orc_set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < npix; ++i) {
+        double s[3];
+        orc_sct_pixel(co, rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2], s);
+        Lo[i] = s[0];
+        Ao[i] = s[1];
+        Bo[i] = s[2];
+    }
+}
+
+/* Eq. equ_sct_rgb: SCT -> RGB codes (real valued, not clamped). */
+ORC_API void orc_sct_inverse(const double s[3], double rgb[3])
+{
+    rgb[0] = s[0] * sin(s[1]) * cos(s[2]);
+    rgb[1] = s[0] * sin(s[1]) * sin(s[2]);
+    rgb[2] = s[0] * cos(s[1]);
+}
+
+/* ---------------------------------------------------------------- 3D LUTs */
+
+/* Packing (Section "Comparison with 3D Lookup Table Interpolation Methods"):
+ * node (i, j, k) holds the exact CIELAB of k' = (i, j, k)/(N-1), rounded to
+ * FP32.  Layout lut[((i*N + j)*N + k)*3 + c], R outermost. */
+ORC_API void orc_lut_build(const orc_rgbdef *d, int N, float *lut)
+{
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j)
+            for (int k = 0; k < N; ++k) {
+                double lab[3];
+                double s = 255.0 / (double)(N - 1);
+                orc_cielab_pixel(d, 0, NULL, 0, NULL, 0, i * s, j * s, k * s, lab);
+                for (int c = 0; c < 3; ++c)
+                    lut[((int64_t)(i * N + j) * N + k) * 3 + c] = (float)lab[c];
+            }
+}
+
+/* Extraction: integer cell index and remainder of a code along one axis. */
+static void orc_lut_locate(int v, int N, int *idx, int *rem)
+{
+    int s = v * (N - 1);
+    *idx = s / 255;
+    *rem = s % 255;
+    if (*idx == N - 1) {   /* v = 255 */
+        *idx = N - 2;
+        *rem = 255;
+    }
+}
+
+enum { ORC_TRILINEAR = 0, ORC_PRISM = 1, ORC_PYRAMID = 2, ORC_TETRA = 3 };
+
+/* Interpolation of one pixel.  Writes the three values and returns the
+ * selection id: (node index of the cell's lower corner) * 8 + simplex id.
+ * Corner cXYZ has X = R offset, Y = G offset, Z = B offset.  Weights are the
+ * classic forms of each method (Kang 2006, as the paper cites). */
+ORC_API int orc_lut_interp_pixel(int method, const float *lut, int N,
+                                 int r, int g, int b, double out[3])
+{
+    int ir, ig, ib, rr, rg, rb;
+    orc_lut_locate(r, N, &ir, &rr);
+    orc_lut_locate(g, N, &ig, &rg);
+    orc_lut_locate(b, N, &ib, &rb);
+    double fr = rr / 255.0, fg = rg / 255.0, fb = rb / 255.0;
+    int base = (ir * N + ig) * N + ib;
+    int simplex = 0;
+    for (int ch = 0; ch < 3; ++ch) {
+#define C(x, y, z) ((double)lut[((int64_t)base + (int64_t)(x) * N * N + (int64_t)(y) * N + (z)) * 3 + ch])
+        double c000 = C(0, 0, 0), c001 = C(0, 0, 1), c010 = C(0, 1, 0), c011 = C(0, 1, 1);
+        double c100 = C(1, 0, 0), c101 = C(1, 0, 1), c110 = C(1, 1, 0), c111 = C(1, 1, 1);
+#undef C
+        double v;
+        if (method == ORC_TRILINEAR) {
+            v = c000 * (1 - fr) * (1 - fg) * (1 - fb) + c001 * (1 - fr) * (1 - fg) * fb
+              + c010 * (1 - fr) * fg * (1 - fb) + c011 * (1 - fr) * fg * fb
+              + c100 * fr * (1 - fg) * (1 - fb) + c101 * fr * (1 - fg) * fb
+              + c110 * fr * fg * (1 - fb) + c111 * fr * fg * fb;
+            simplex = 0;
+        } else if (method == ORC_PRISM) {
+            /* prism axis along R; the G-B face is split on its diagonal */
+            if (rg >= rb) {
+                v = c000 + (c010 - c000) * fg + (c011 - c010) * fb + (c100 - c000) * fr
+                  + (c110 - c100 - c010 + c000) * fg * fr + (c111 - c110 - c011 + c010) * fb * fr;
+                simplex = 0;
+            } else {
+                v = c000 + (c011 - c001) * fg + (c001 - c000) * fb + (c100 - c000) * fr
+                  + (c111 - c101 - c011 + c001) * fg * fr + (c101 - c100 - c001 + c000) * fb * fr;
+                simplex = 1;
+            }
+        } else if (method == ORC_PYRAMID) {
+            /* apex c111; the base is the cube face of the smallest fraction */
+            if (rb <= rr && rb <= rg) {          /* base B = 0 */
+                v = c000 + (c111 - c110) * fb + (c100 - c000) * fr + (c010 - c000) * fg
+                  + (c110 - c100 - c010 + c000) * fr * fg;
+                simplex = 0;
+            } else if (rg <= rr && rg <= rb) {   /* base G = 0 */
+                v = c000 + (c111 - c101) * fg + (c100 - c000) * fr + (c001 - c000) * fb
+                  + (c101 - c100 - c001 + c000) * fr * fb;
+                simplex = 1;
+            } else {                             /* base R = 0 */
+                v = c000 + (c111 - c011) * fr + (c010 - c000) * fg + (c001 - c000) * fb
+                  + (c011 - c001 - c010 + c000) * fg * fb;
+                simplex = 2;
+            }
+        } else {
+            /* tetrahedral: six orderings of (rem_R, rem_G, rem_B) */
+            if (rr >= rg && rg >= rb) {
+                v = c000 + (c100 - c000) * fr + (c110 - c100) * fg + (c111 - c110) * fb;
+                simplex = 0;
+            } else if (rr >= rb && rb > rg) {
+                v = c000 + (c100 - c000) * fr + (c111 - c101) * fg + (c101 - c100) * fb;
+                simplex = 1;
+            } else if (rb > rr && rr >= rg) {
+                v = c000 + (c101 - c001) * fr + (c111 - c101) * fg + (c001 - c000) * fb;
+                simplex = 2;
+            } else if (rg > rr && rr >= rb) {
+                v = c000 + (c110 - c010) * fr + (c010 - c000) * fg + (c111 - c110) * fb;
+                simplex = 3;
+            } else if (rg >= rb && rb > rr) {
+                v = c000 + (c111 - c011) * fr + (c010 - c000) * fg + (c011 - c010) * fb;
+                simplex = 4;
+            } else {
+                v = c000 + (c111 - c011) * fr + (c011 - c001) * fg + (c001 - c000) * fb;
+                simplex = 5;
+            }
+        }
+        out[ch] = v;
+    }
+    return base * 8 + simplex;
+}
+
+ORC_API void orc_lut_interp(int method, const float *lut, int N,
+                            const uint8_t *rgb, int64_t npix,
+                            double *o0, double *o1, double *o2, int32_t *sel, int nthreads)
+{
+    orc_set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < npix; ++i) {
+        double v[3];
+        int s = orc_lut_interp_pixel(method, lut, N, rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2], v);
+        o0[i] = v[0];
+        o1[i] = v[1];
+        o2[i] = v[2];
+        if (sel) sel[i] = s;
+    }
+}
+
+/* ------------------------------------------- statistics over the RGB cube */
+/* Section "Calculation of the Color Space Transformation Errors": average and
+ * maximum transformation error over every 24-bit colour. */
+
+/* Fractions of the cube with t_c > 0.008856 (Eq. equ_cbrt_prob). */
+ORC_API void orc_cube_cbrt_probs(const orc_rgbdef *d, double probs[3])
+{
+    int64_t cnt[3] = {0, 0, 0};
+    int64_t c0 = 0, c1 = 0, c2 = 0;
+#pragma omp parallel for reduction(+:c0, c1, c2) schedule(static)
+    for (int r = 0; r < 256; ++r)
+        for (int g = 0; g < 256; ++g)
+            for (int b = 0; b < 256; ++b) {
+                double t[3];
+                orc_rgb_to_t(d, r, g, b, t);
+                c0 += t[0] > 0.008856;
+                c1 += t[1] > 0.008856;
+                c2 += t[2] > 0.008856;
+            }
+    cnt[0] = c0; cnt[1] = c1; cnt[2] = c2;
+    for (int c = 0; c < 3; ++c) probs[c] = (double)cnt[c] / 16777216.0;
+}
+
+/* P(B/L >= 0.5) and P(not (R = G = 0)) (Eq. equ_sct_arcsin_arccos_prob,
+ * equ_sct_b_prob), on the codes. */
+ORC_API void orc_cube_sct_probs(double probs[2])
+{
+    int64_t na = 0, nb = 0;
+#pragma omp parallel for reduction(+:na, nb) schedule(static)
+    for (int r = 0; r < 256; ++r)
+        for (int g = 0; g < 256; ++g)
+            for (int b = 0; b < 256; ++b) {
+                double L = sqrt((double)(r * r + g * g + b * b));
+                if (L > 0.0 && b / L >= 0.5) na++;
+                if (!(r == 0 && g == 0)) nb++;
+            }
+    probs[0] = (double)na / 16777216.0;
+    probs[1] = (double)nb / 16777216.0;
+}
+
+/* CIELAB: Delta E*ab between the MACT and the exact transform. */
+ORC_API void orc_cube_eps_cielab(const orc_rgbdef *d, const double *p, int n,
+                                 const double *q, int m, double out[2])
+{
+    double sum = 0.0, mx = 0.0;
+#pragma omp parallel for reduction(+:sum) reduction(max:mx) schedule(static)
+    for (int r = 0; r < 256; ++r)
+        for (int g = 0; g < 256; ++g)
+            for (int b = 0; b < 256; ++b) {
+                double e[3], a[3];
+                orc_cielab_pixel(d, 0, NULL, 0, NULL, 0, r, g, b, e);
+                orc_cielab_pixel(d, 1, p, n, q, m, r, g, b, a);
+                double de = orc_delta_e(e, a);
+                sum += de;
+                if (de > mx) mx = de;
+            }
+    out[0] = sum / 16777216.0;
+    out[1] = mx;
+}
+
+/* HSI: D_HSI between Kender-with-P_n and the exact transform. */
+ORC_API void orc_cube_eps_hsi(const double *c, int n, double out[2])
+{
+    double sum = 0.0, mx = 0.0;
+#pragma omp parallel for reduction(+:sum) reduction(max:mx) schedule(static)
+    for (int r = 0; r < 256; ++r)
+        for (int g = 0; g < 256; ++g)
+            for (int b = 0; b < 256; ++b) {
+                double e[3], a[3];
+                orc_hsi_pixel(0, NULL, 0, r, g, b, e);
+                orc_hsi_pixel(1, c, n, r, g, b, a);
+                double dd = orc_d_hsi(e, a);
+                sum += dd;
+                if (dd > mx) mx = dd;
+            }
+    out[0] = sum / 16777216.0;
+    out[1] = mx;
+}
+
+/* SCT: approximate SCT -> inverse SCT -> exact CIELAB, Delta E*ab against
+ * the exact CIELAB of the pixel (Section "Color Space Description" of SCT). */
+ORC_API void orc_cube_eps_sct(const orc_rgbdef *d, const orc_sct_coeffs *co, double out[2])
+{
+    double sum = 0.0, mx = 0.0;
+#pragma omp parallel for reduction(+:sum) reduction(max:mx) schedule(static)
+    for (int r = 0; r < 256; ++r)
+        for (int g = 0; g < 256; ++g)
+            for (int b = 0; b < 256; ++b) {
+                double s[3], back[3], e[3], a[3];
+                orc_sct_pixel(co, r, g, b, s);
+                orc_sct_inverse(s, back);
+                orc_cielab_pixel(d, 0, NULL, 0, NULL, 0, back[0], back[1], back[2], a);
+                orc_cielab_pixel(d, 0, NULL, 0, NULL, 0, r, g, b, e);
+                double de = orc_delta_e(e, a);
+                sum += de;
+                if (de > mx) mx = de;
+            }
+    out[0] = sum / 16777216.0;
+    out[1] = mx;
+}
+
+/* LUT interpolation: Delta E*ab against the exact CIELAB. */
+ORC_API void orc_cube_eps_lut(const orc_rgbdef *d, int method, const float *lut, int N, double out[2])
+{
+    double sum = 0.0, mx = 0.0;
+#pragma omp parallel for reduction(+:sum) reduction(max:mx) schedule(static)
+    for (int r = 0; r < 256; ++r)
+        for (int g = 0; g < 256; ++g)
+            for (int b = 0; b < 256; ++b) {
+                double e[3], a[3];
+                orc_lut_interp_pixel(method, lut, N, r, g, b, a);
+                orc_cielab_pixel(d, 0, NULL, 0, NULL, 0, r, g, b, e);
+                double de = orc_delta_e(e, a);
+                sum += de;
+                if (de > mx) mx = de;
+            }
+    out[0] = sum / 16777216.0;
+    out[1] = mx;
+}
