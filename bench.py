@@ -1,0 +1,384 @@
+"""Benchmark of the MACT per-pixel hot path on GB300.
+
+Workload (one step): every 24-bit colour (2^24 pixels, lexicographic, one
+4096 x 4096 uint8 image) converted by each per-pixel row of the hot path:
+MACT RGB->CIELAB (4,4), HSI (n=5), SCT (5,5,5); the exact (libm) forms of
+the three; and trilinear / prism / pyramidal / tetrahedral interpolation in
+17^3 and 33^3 FP32 LUTs -- 14 conversions, FP32 planar output.
+
+value = pixel-conversions per second over the whole step (14 x 2^24 pixels
+per step per GPU), in Gpix/s; the MACT CIELAB row's own Gpix/s and HBM
+roofline fraction are reported under "rows" and "roofline_mact_cielab".
+Inputs rotate over 8 distinct copies of the cube (400 MB > the 129 MB L2),
+so no row reads its input from L2.
+
+--impl reference times the FP64 CPU oracle (the deliberately slow reference
+arm) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PIX = 1 << 24
+IN_COPIES = 8
+METRIC = "Gpix/s and % of HBM roofline (MACT RGB→CIELAB); served p99 vs plain, same ΔE"
+WORKLOAD = ("exhaustive RGB cube: 2^24 uint8 triplets (4096x4096, lexicographic) through MACT "
+            "CIELAB(4,4)/HSI(5)/SCT(5,5,5), exact CIELAB/HSI/SCT, and tri/prism/pyr/tet from 17^3 and "
+            "33^3 FP32 LUTs; FP32 planar out; 14 conversions per step")
+
+ROWS = ([("mact_cielab", "mact", "cielab"), ("mact_hsi", "mact", "hsi"), ("mact_sct", "mact", "sct"),
+         ("exact_cielab", "exact", "cielab"), ("exact_hsi", "exact", "hsi"), ("exact_sct", "exact", "sct")] +
+        [("lut%d_%s" % (n, m), "lut", (m, n)) for n in (17, 33)
+         for m in ("trilinear", "prism", "pyramid", "tetra")])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001 - fall back to the recipe's figure
+        return 6800.0, "fallback"
+
+
+def traffic_table():
+    """Per-launch DRAM bytes from the committed ncu summary, keyed by row,
+    with the source hash the capture was taken on (None if stale/absent)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    out = {}
+    if not os.path.exists(path):
+        return out
+    cur = source_hash()
+    for line in open(path):
+        line = line.split("#", 1)[0].split()
+        if len(line) == 3 and line[2] == cur:
+            out[line[0]] = float(line[1])
+    return out
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1009_0854_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:  # noqa: BLE001 - no nvidia-smi: no clock record
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1009_0854_gb300 import mact, synth
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    h_mact = mact.mact_create()
+    h_exact = mact.mact_create(exact=1)
+    cube = synth.rgb_cube()
+    cube_h = torch.from_numpy(cube)
+    inputs = [cube_h.to(dev) for _ in range(IN_COPIES)]
+    luts = {n: mact.mact_lut_build(h_mact, n, device=dev) for n in (17, 33)}
+    outs = {name: torch.empty((3, 4096, 4096), dtype=torch.float32, device=dev) for name, _, _ in ROWS}
+    torch.cuda.synchronize()
+
+    def run_row(name, kind, arg, rgb, out):
+        if kind == "mact":
+            mact.mact_convert(h_mact, rgb, arg, out=out, stream=stream)
+        elif kind == "exact":
+            mact.mact_convert(h_exact, rgb, arg, out=out, stream=stream)
+        else:
+            m, n = arg
+            mact.mact_lut_interp(h_mact, m, luts[n], rgb, out=out.view(3, -1), stream=stream)
+
+    ev = {name: [] for name, _, _ in ROWS}
+
+    def step(i, timed):
+        for r, (name, kind, arg) in enumerate(ROWS):
+            rgb = inputs[(i * len(ROWS) + r) % IN_COPIES]
+            if timed:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            run_row(name, kind, arg, rgb, outs[name])
+            if timed:
+                e1.record(stream)
+                ev[name].append((e0, e1))
+
+    for i in range(args.warmup):
+        step(i, False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.25)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i, True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    launches = args.steps * len(ROWS)
+
+    row_ms = {name: statistics.mean(a.elapsed_time(b) for a, b in ev[name]) for name in ev}
+    hbm, peak_kind = peaks()
+    traffic = traffic_table()
+    bytes_px = 3 + 12
+
+    def roof(name):
+        t = row_ms[name] * 1e-3
+        achieved = PIX * bytes_px / t / 1e9
+        tr = traffic.get(name)
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": tr, "kernel": name,
+                "peak_source": peak_kind, "ms_per_launch": round(row_ms[name], 5)}
+
+    dominant = max(row_ms, key=row_ms.get)
+    rows = {name: {"gpix_s": round(PIX / (row_ms[name] * 1e-3) / 1e9, 2), "ms": round(row_ms[name], 5),
+                   "hbm_frac": round(PIX * bytes_px / (row_ms[name] * 1e-3) / 1e9 / hbm, 4)}
+            for name in row_ms}
+
+    # end to end through the C ABI with host buffers: pinned H2D of the input,
+    # every row, D2H of every output plane, all inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pin_in = cube_h.pin_memory()
+        pin_out = {name: torch.empty((3, 4096, 4096), dtype=torch.float32).pin_memory() for name, _, _ in ROWS}
+        dev_in = inputs[0]
+
+        def e2e_step():
+            dev_in.copy_(pin_in, non_blocking=True)
+            for name, kind, arg in ROWS:
+                run_row(name, kind, arg, dev_in, outs[name])
+            for name, _, _ in ROWS:
+                pin_out[name].copy_(outs[name], non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        k = max(2, args.steps // 4)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ems = a.elapsed_time(b) / k
+        if world > 1:
+            tt = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ems = float(tt.item())
+        e2e = {"value": round(world * len(ROWS) * PIX / (ems * 1e-3) / 1e9, 3), "unit": "Gpix/s",
+               "h2d_bytes_per_step": 3 * PIX, "d2h_bytes_per_step": len(ROWS) * 12 * PIX,
+               "ms_per_step": round(ems, 4)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_pixels)
+
+    if rank == 0:
+        value = world * len(ROWS) * PIX / (ms / args.steps * 1e-3) / 1e9
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Gpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pixels_per_conversion": PIX, "conversions_per_step": len(ROWS),
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs rotate over %d distinct 50 MB copies (400 MB > 129 MB L2)" % IN_COPIES},
+            "roofline": roof(dominant),
+            "roofline_mact_cielab": roof("mact_cielab"),
+            "mact_cielab_gpix_s": rows["mact_cielab"]["gpix_s"],
+            "rows": rows,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------- oracle (CPU) arm
+
+def _oracle_rows(rgb, luts, nthreads):
+    import oracle as O
+    for name, kind, arg in ROWS:
+        if kind == "mact":
+            if arg == "cielab":
+                O.cielab(rgb, nthreads=nthreads)
+            elif arg == "hsi":
+                O.hsi(rgb, nthreads=nthreads)
+            else:
+                O.sct(rgb, nthreads=nthreads)
+        elif kind == "exact":
+            if arg == "cielab":
+                O.cielab(rgb, exact=True, nthreads=nthreads)
+            elif arg == "hsi":
+                O.hsi(rgb, mode="exact", nthreads=nthreads)
+            else:
+                O.sct(rgb, exact=True, nthreads=nthreads)
+        else:
+            m, n = arg
+            O.lut_interp(m, luts[n], rgb, nthreads=nthreads)
+
+
+def cpu_baseline(npix):
+    """The FP64 oracle, as it stands, on the host cores: the first npix
+    colours of the cube through all 14 conversions."""
+    import oracle as O
+    from paper_1009_0854_gb300 import synth
+    cores = O.max_threads()
+    rgb = synth.rgb_cube().reshape(-1, 3)[:npix].copy()
+    luts = {n: O.lut_build(n) for n in (17, 33)}
+    _oracle_rows(rgb[:4096], luts, cores)
+    t = time.perf_counter()
+    _oracle_rows(rgb, luts, cores)
+    dt = time.perf_counter() - t
+    return {"value": round(len(ROWS) * npix / dt / 1e9, 6), "unit": "Gpix/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d cube colours x %d conversions (%.1f s wall)" % (npix, len(ROWS), dt)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1009_0854_gb300 import synth
+    cores = O.max_threads()
+    npix = args.ref_pixels
+    rgb_all = synth.rgb_cube().reshape(-1, 3)
+    luts = {n: O.lut_build(n) for n in (17, 33)}
+    times = []
+    for i in range(args.warmup + args.steps):
+        off = (i * npix) % PIX
+        rgb = rgb_all[off:off + npix].copy()
+        t = time.perf_counter()
+        _oracle_rows(rgb, luts, cores)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+    sec = sum(times) / len(times)
+    value = len(ROWS) * npix / sec / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gpix/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pixels_per_conversion_sampled": npix,
+                   "conversions_per_step": len(ROWS)},
+        "cpu_baseline": {"value": round(value, 6), "unit": "Gpix/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d consecutive cube colours per step x %d conversions" % (npix, len(ROWS))},
+        "e2e": {"value": round(value, 6), "unit": "Gpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mact", choices=["mact", "reference"])
+    ap.add_argument("--cpu-pixels", type=int, default=PIX)
+    ap.add_argument("--ref-pixels", type=int, default=1 << 22)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * mact.h -- C ABI of libmact.so: MACT colour-space transforms and 3D-LUT
+ * interpolation on an NVIDIA GB300 (sm_103a).
+ *
+ * MACT (Celebi, Kingravi & Celiker, "Fast Color Space Transformations Using
+ * Minimax Approximations") replaces the elementary functions of three RGB
+ * transforms by minimax polynomials or rationals:
+ *   RGB -> CIELAB   cube root -> p_n(t)/q_m(t)          (Tables tab_cbrt_poly,
+ *                                                        tab_cbrt_rat)
+ *   RGB -> HSI      arctan(sqrt(3) x) -> P_n(|x|)       (Table tab_arctan)
+ *   RGB -> SCT      arccos, arctan -> polynomials       (Tables tab_arcsin,
+ *                                                        tab_arccos, tab_f, tab_g)
+ * and compares them with trilinear, prism, pyramidal and tetrahedral
+ * interpolation in a 3D lookup table (Section "Comparison with 3D Lookup
+ * Table Interpolation Methods").
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* and the pointers inside mact_image are DEVICE
+ *    pointers on the current CUDA device, except where a function says host.
+ *    The caller owns every image, LUT and output buffer; the library never
+ *    frees them.
+ *  - A handle owns a small device block (gamma table, coefficients) created on
+ *    the device that is current when mact_create is called; use the handle on
+ *    that device only.
+ *  - Work is enqueued on the given stream (a cudaStream_t cast to
+ *    mact_stream; NULL is the legacy default stream) and returns before it
+ *    completes.  Argument errors are reported synchronously and enqueue
+ *    nothing.  A CUDA launch error returns MACT_E_CUDA; the text of the last
+ *    error of the calling thread is available from mact_last_error().
+ *  - No C++ exception crosses this interface.
+ *  - Input is interleaved 8-bit R'G'B' (3 bytes per pixel).  Output is three
+ *    planes, FP32 or FP16:
+ *      CIELAB: L*, a*, b* in CIE units (white = 100, 0, 0);
+ *      HSI:    H in radians [0, 2 pi), S and I in [0, 1] with R = R'/255;
+ *              H = 0 where max == min (hue undefined), S = 0 for black;
+ *      SCT:    L in 8-bit code units [0, 441.7], angle A and angle B in
+ *              radians; black gives (0, 0, 0), R = G = 0 gives B = 0.
+ */
+#ifndef MACT_H
+#define MACT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mact_ctx *mact_handle;
+typedef struct mact_server *mact_server_t;
+typedef void *mact_stream; /* cudaStream_t */
+
+typedef enum {
+    MACT_OK = 0,
+    MACT_E_INVAL = -1,       /* bad argument: null pointer, size, enum, degree */
+    MACT_E_NOMEM = -2,       /* device memory or admission budget exhausted */
+    MACT_E_CUDA = -3,        /* a CUDA call failed; see mact_last_error() */
+    MACT_E_UNSUPPORTED = -4, /* valid request this build does not implement */
+    MACT_E_TIMEOUT = -5,     /* a bounded wait ran out */
+    MACT_E_BUSY = -6         /* no free slot; retry later */
+} mact_status;
+
+typedef enum { MACT_CIELAB = 0, MACT_HSI = 1, MACT_SCT = 2 } mact_space;
+typedef enum { MACT_F32 = 0, MACT_F16 = 1 } mact_dtype;
+typedef enum { MACT_TRILINEAR = 0, MACT_PRISM = 1, MACT_PYRAMID = 2, MACT_TETRA = 3 } mact_interp;
+
+/* Source RGB definition (Eq. equ_rgb_lin, equ_rgb_xyz and the D65 white of
+ * Section "Color Space Description", CIELAB).  Inverse gamma:
+ *   k = k'/slope                                  if k' < threshold
+ *   k = ((k' + offset)/(1 + offset))^exponent     otherwise,   k' = code/255.
+ * rgb_to_xyz is row-major (X row first).  white = (X0, Y0, Z0). */
+typedef struct {
+    double gamma_threshold; /* 0.081 */
+    double gamma_slope;     /* 4.5 */
+    double gamma_offset;    /* 0.099 */
+    double gamma_exponent;  /* 1/0.45 */
+    double rgb_to_xyz[9];   /* BT.709 */
+    double white[3];        /* D65: 0.950456, 1.0, 1.089058 */
+} mact_rgb_def;
+
+/* Transform configuration.
+ *  exact      0: MACT approximants; 1: the exact functions (cbrtf, atan2f,
+ *             acosf, sqrtf) -- the "plain" form the paper times as "exact".
+ *  lab_n, lab_m  cube-root approximant: lab_m > 0 selects the rational (n, m)
+ *             of Table tab_cbrt_rat (2 <= n, m <= 4, the nine printed pairs);
+ *             lab_m == 0 selects the polynomial of degree lab_n (2..5) of
+ *             Table tab_cbrt_poly.  Default (4, 4).
+ *  hsi_n      degree 2..5 of the arctan(sqrt(3) x) polynomial.  Default 5.
+ *  hsi_coeffs 0: minimax fit on [0, 1], computed by the library at create
+ *             time (|x| = 1 occurs in Kender's formula); 1: Table tab_arctan
+ *             as printed (n = 2 with a2 = -7.497879e-01).  Default 0.
+ *  sct_n, sct_m, sct_r  degrees (4 or 5) of the arcsin, arccos and f/g
+ *             polynomials (Tables tab_arcsin, tab_arccos, tab_f, tab_g).
+ *             Default (5, 5, 5). */
+typedef struct {
+    mact_rgb_def rgb;
+    int32_t exact;
+    int32_t lab_n, lab_m;
+    int32_t hsi_n;
+    int32_t hsi_coeffs;
+    int32_t sct_n, sct_m, sct_r;
+} mact_config;
+
+/* One image.  rgb: device pointer to height rows of width interleaved
+ * pixels, rows pitch_bytes apart (>= 3*width).  out[c]: device pointers to
+ * the three output planes, rows out_pitch_elems elements apart (>= width),
+ * element type given by dtype.  space: mact_space; dtype: mact_dtype.
+ * Fastest when rgb is 16-byte aligned, pitch_bytes == 3*width,
+ * out_pitch_elems == width and every out[c] is 16-byte aligned; any other
+ * layout is accepted and handled by a slower tail path. */
+typedef struct {
+    const uint8_t *rgb;
+    int64_t width, height, pitch_bytes;
+    int32_t space;
+    int32_t dtype;
+    void *out[3];
+    int64_t out_pitch_elems;
+} mact_image;
+
+/* Fill *cfg with the paper's defaults: BT.709 + D65, CIELAB (4,4), HSI n=5 on
+ * [0,1], SCT (5,5,5), approximants on. */
+void mact_config_default(mact_config *cfg);
+
+/* Validate *cfg and build a handle on the current device.  Rejects unknown
+ * degrees and any RGB definition for which white maps to t > 1 + 1e-6 or a
+ * non-positive white component (the cube-root approximants are fitted on
+ * [0.008856, 1], Figure fig_cbrt).  Allocates about 4 KB of device memory.
+ * *out is written only on success. */
+mact_status mact_create(const mact_config *cfg, mact_handle *out);
+
+/* Free the handle's device block.  Work already enqueued with the handle must
+ * have completed (the call synchronises the device before freeing). */
+mact_status mact_destroy(mact_handle h);
+
+/* Convert one image to img->space (Sections "CIELAB Color Space", "HSI
+ * Color Space", "Spherical Coordinate Transform").  Asynchronous on stream.
+ * width or height 0 is a valid empty image (nothing is launched). */
+mact_status mact_convert(mact_handle h, const mact_image *img, mact_stream stream);
+
+/* Convert count images of any sizes, spaces and dtypes in ONE launch of a
+ * persistent kernel that walks a tile work list (the batched form).  The
+ * work list lives in a device buffer owned by the handle, grown on demand;
+ * calls on one handle from several streams are serialised by the library.
+ * Result of each image equals mact_convert of that image. */
+mact_status mact_convert_batch(mact_handle h, const mact_image *imgs, int32_t count,
+                               mact_stream stream);
+
+/* Packing step of the LUT methods: fill d_lut (n^3 x 3 FP32, layout
+ * d_lut[((i*n + j)*n + k)*3 + c], R outermost) with the exact CIELAB of the
+ * node codes 255*(i,j,k)/(n-1), computed in FP32 with cbrtf.  2 <= n <= 64. */
+mact_status mact_lut_build(mact_handle h, int32_t n, float *d_lut, mact_stream stream);
+
+/* Extraction + interpolation (Section "Comparison with 3D Lookup Table
+ * Interpolation Methods"): for each of npix interleaved pixels of d_rgb, the
+ * cell along each axis is idx = v(n-1) div 255 with remainder
+ * rem = v(n-1) mod 255 (v = 255 uses idx = n-2, rem = 255) and the fraction
+ * is rem/255; method picks the 8-node trilinear, 6-node prism (axis R),
+ * 5-node pyramid (apex at the far corner, base = face of the smallest
+ * fraction) or 4-node tetrahedron (ordering of the remainders).  The three
+ * interpolated values go to d_out[0..2] (FP32, npix each).  If d_sel is not
+ * NULL it receives, per pixel, (lower-corner node index)*8 + simplex id.
+ * d_lut layout as in mact_lut_build, 2 <= n <= 64. */
+mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, int32_t n,
+                            const uint8_t *d_rgb, int64_t npix, float *const d_out[3],
+                            int32_t *d_sel, mact_stream stream);
+
+/* Message for a status code (static storage). */
+const char *mact_strerror(mact_status st);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char *mact_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MACT_H */

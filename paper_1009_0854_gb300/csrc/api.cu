@@ -1,0 +1,372 @@
+// api.cu -- the exported C ABI of libmact.so (include/mact.h): argument
+// validation, handle state, work lists, and dispatch to the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace mact {
+
+bool hsi_unit_interval_fit(int n, double *coef6, double *err);
+
+// ---- coefficient tables of the paper (ascending powers) -------------------
+
+// Table tab_cbrt_poly: t^(1/3) ~ p_n(t).
+static const double kCbrtPoly[4][6] = {
+    {1.268979e-01, 2.393873, -1.647669, 0, 0, 0},
+    {9.787826e-02, 4.057495, -7.388864, 4.331370, 0, 0},
+    {8.111133e-02, 5.926004, -2.017165e+01, 2.833070e+01, -1.324728e+01, 0},
+    {7.002910e-02, 7.961214, -4.329352e+01, 1.063182e+02, -1.135685e+02, 4.358268e+01},
+};
+
+// Table tab_cbrt_rat: t^(1/3) ~ p_n(t)/q_m(t) on [0.008856, 1].
+struct RatRow { int n, m; double p[5], q[5]; };
+static const RatRow kCbrtRat[9] = {
+    {2, 2, {6.309655e-03, 5.785782e-01, 1.591005}, {4.482646e-02, 1.175862, 9.596879e-01}},
+    {2, 3, {2.500705e-03, 3.447113e-01, 1.942708}, {1.978701e-02, 8.542797e-01, 1.664540, -2.503267e-01}},
+    {3, 2, {1.776519e-03, 2.632323e-01, 1.751297, 3.836709e-01}, {1.432256e-02, 6.779998e-01, 1.706260}},
+    {2, 4, {1.317899e-03, 2.390113e-01, 2.099395},
+     {1.124254e-02, 6.726679e-01, 2.184656, -7.511150e-01, 2.229717e-01}},
+    {3, 3, {4.370889e-04, 9.526952e-02, 1.252009, 1.302733}, {3.912364e-03, 2.954084e-01, 1.717143, 6.343408e-01}},
+    {4, 2, {7.589302e-04, 1.519784e-01, 1.663584, 8.368075e-01, -1.657269e-01},
+     {6.644723e-03, 4.506424e-01, 2.030622}},
+    {3, 4, {1.683667e-04, 4.667675e-02, 9.106812e-01, 1.810577},
+     {1.610864e-03, 1.617974e-01, 1.494070, 1.218468, -1.079451e-01}},
+    {4, 3, {1.349673e-04, 3.832079e-02, 7.870174e-01, 1.799062, 2.071170e-01},
+     {1.299250e-03, 1.345420e-01, 1.330358, 1.365369}},
+    {4, 4, {3.927283e-05, 1.392318e-02, 4.114739e-01, 1.734853, 8.679223e-01},
+     {4.022100e-04, 5.414536e-02, 8.221526e-01, 1.800167, 3.513617e-01}},
+};
+
+// Table tab_arctan as printed (n = 2 with a2 negative: the printed plus sign
+// gives an error of 1.5 at x = 1 and is read as a typesetting slip).
+static const double kHsiPrinted[4][6] = {
+    {5.959793e-03, 1.782975, -7.497879e-01, 0, 0, 0},
+    {-3.654076e-03, 1.884080, -9.805583e-01, 1.430580e-01, 0, 0},
+    {-1.286369e-03, 1.796716, -4.958969e-01, -6.927404e-01, 4.421541e-01, 0},
+    {-1.801283e-04, 1.739333, -2.039848e-02, -2.065512, 2.052837, -6.591729e-01},
+};
+
+// Tables tab_arcsin, tab_arccos, tab_f, tab_g (degrees 4 and 5).
+static const double kSctArcsin[2][6] = {
+    {2.097797e-05, 1.412840, 1.429881e-02, 6.704361e-02, 6.909677e-02, 0},
+    {-2.370048e-06, 1.414434, -3.300037e-03, 1.354670e-01, -3.994259e-02, 6.099502e-02},
+};
+static const double kSctArccos[2][6] = {
+    {1.570786, -9.990285e-01, -1.429899e-02, -9.481335e-02, -1.381942e-01, 0},
+    {1.570798, -1.000156, 3.299810e-03, -1.915780e-01, 7.988231e-02, -1.725177e-01},
+};
+static const double kSctF[2][6] = {
+    {-1.036508e-04, 1.003740, -1.773538e-02, -3.390563e-01, 1.386796e-01, 0},
+    {2.073866e-05, 9.982666e-01, 2.352573e-02, -4.506862e-01, 2.635050e-01, -4.920822e-02},
+};
+static const double kSctG[2][6] = {
+    {1.570917, -1.004004, 1.885694e-02, 3.373159e-01, -1.377930e-01, 0},
+    {1.570769, -9.981253e-01, -2.440212e-02, 4.528921e-01, -2.659181e-01, 5.016228e-02},
+};
+
+// ---- errors ----------------------------------------------------------------
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+mact_status cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return MACT_OK;
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MACT_E_NOMEM : MACT_E_CUDA;
+}
+
+static mact_status inval(const char *msg)
+{
+    set_error(msg);
+    return MACT_E_INVAL;
+}
+
+// ---- configuration ---------------------------------------------------------
+
+static mact_status build_coeffs(const mact_config &cfg, Coeffs &co)
+{
+    std::memset(&co, 0, sizeof(co));
+    const mact_rgb_def &d = cfg.rgb;
+    for (int c = 0; c < 3; ++c) {
+        if (!(d.white[c] > 0.0) || !std::isfinite(d.white[c])) return inval("white point must be positive");
+        double rowsum = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            if (!std::isfinite(d.rgb_to_xyz[3 * c + j])) return inval("rgb_to_xyz must be finite");
+            co.m[3 * c + j] = (float)(d.rgb_to_xyz[3 * c + j] / d.white[c]);
+            rowsum += d.rgb_to_xyz[3 * c + j];
+        }
+        // white (k = 1,1,1) must map to t <= 1: the cube-root fits live on [0.008856, 1]
+        if (rowsum / d.white[c] > 1.0 + 1e-6) return inval("RGB definition maps white above the reference white");
+    }
+    if (!(d.gamma_slope > 0.0) || !(d.gamma_exponent > 0.0) || !(d.gamma_offset > -1.0) ||
+        !std::isfinite(d.gamma_threshold))
+        return inval("invalid gamma parameters");
+
+    // cube root
+    if (cfg.lab_m == 0) {
+        if (cfg.lab_n < 2 || cfg.lab_n > 5) return inval("lab_n must be 2..5 for the polynomial (lab_m = 0)");
+        for (int i = 0; i < 6; ++i) co.lab_d[i] = (float)kCbrtPoly[cfg.lab_n - 2][i];
+        co.lab_rational = 0;
+    } else {
+        const RatRow *row = nullptr;
+        for (const RatRow &r : kCbrtRat)
+            if (r.n == cfg.lab_n && r.m == cfg.lab_m) row = &r;
+        if (!row) return inval("(lab_n, lab_m) is not one of the nine rationals of the cube-root table");
+        double p[5] = {0, 0, 0, 0, 0}, q[5] = {0, 0, 0, 0, 0};
+        for (int i = 0; i <= row->n; ++i) p[i] = row->p[i];
+        for (int i = 0; i <= row->m; ++i) q[i] = row->q[i];
+        for (int i = 0; i < 5; ++i) {
+            co.lab_d[i] = (float)(p[i] - q[i]);   // f = 1 + (p - q)/q
+            co.lab_q[i] = (float)q[i];
+        }
+        co.lab_rational = 1;
+    }
+
+    // HSI
+    if (cfg.hsi_n < 2 || cfg.hsi_n > 5) return inval("hsi_n must be 2..5");
+    if (cfg.hsi_coeffs == 0) {
+        double c[6], e = 0.0;
+        if (!hsi_unit_interval_fit(cfg.hsi_n, c, &e)) return inval("Remez fit of arctan(sqrt(3)x) failed");
+        for (int i = 0; i < 6; ++i) co.hsi[i] = (float)c[i];
+    } else if (cfg.hsi_coeffs == 1) {
+        for (int i = 0; i < 6; ++i) co.hsi[i] = (float)kHsiPrinted[cfg.hsi_n - 2][i];
+    } else {
+        return inval("hsi_coeffs must be 0 (fit on [0,1]) or 1 (as printed)");
+    }
+
+    // SCT
+    auto deg45 = [](int v) { return v == 4 || v == 5; };
+    if (!deg45(cfg.sct_n) || !deg45(cfg.sct_m) || !deg45(cfg.sct_r)) return inval("sct degrees must be 4 or 5");
+    for (int i = 0; i < 6; ++i) {
+        co.sct_p[i] = (float)kSctArcsin[cfg.sct_n - 4][i];
+        co.sct_q[i] = (float)kSctArccos[cfg.sct_m - 4][i];
+        co.sct_f[i] = (float)kSctF[cfg.sct_r - 4][i];
+        co.sct_g[i] = (float)kSctG[cfg.sct_r - 4][i];
+    }
+    return MACT_OK;
+}
+
+// Eq. equ_rgb_lin for the 256 codes, in double, rounded once to FP32.
+static void build_gamma(const mact_rgb_def &d, float *g)
+{
+    for (int v = 0; v < 256; ++v) {
+        double kp = v / 255.0;
+        double k = kp < d.gamma_threshold ? kp / d.gamma_slope
+                                          : std::pow((kp + d.gamma_offset) / (1.0 + d.gamma_offset), d.gamma_exponent);
+        g[v] = (float)k;
+    }
+}
+
+static mact_status check_image(const mact_image *img)
+{
+    if (!img) return inval("image is NULL");
+    if (img->width < 0 || img->height < 0) return inval("negative image size");
+    if (img->space < MACT_CIELAB || img->space > MACT_SCT) return inval("unknown space");
+    if (img->dtype != MACT_F32 && img->dtype != MACT_F16) return inval("unknown dtype");
+    if (img->width == 0 || img->height == 0) return MACT_OK;
+    if (img->width > (int64_t(1) << 40) || img->height > (int64_t(1) << 40)) return inval("image too large");
+    if (!img->rgb || !img->out[0] || !img->out[1] || !img->out[2]) return inval("NULL image pointer");
+    if (img->height > 1 && img->pitch_bytes < 3 * img->width) return inval("pitch_bytes < 3*width");
+    if (img->height > 1 && img->out_pitch_elems < img->width) return inval("out_pitch_elems < width");
+    return MACT_OK;
+}
+
+static ImageDesc make_desc(const mact_image &img)
+{
+    ImageDesc d{};
+    d.rgb = img.rgb;
+    for (int c = 0; c < 3; ++c) d.out[c] = img.out[c];
+    d.space = img.space;
+    d.dtype = img.dtype;
+    const bool contiguous = img.height == 1 || (img.pitch_bytes == 3 * img.width && img.out_pitch_elems == img.width);
+    if (contiguous) {   // one long row: full tiles straddle image rows
+        d.width = img.width * img.height;
+        d.height = (d.width > 0) ? 1 : 0;
+        d.pitch = 3 * d.width;
+        d.opitch = d.width;
+    } else {
+        d.width = img.width;
+        d.height = img.height;
+        d.pitch = img.pitch_bytes;
+        d.opitch = img.out_pitch_elems;
+    }
+    d.tiles_per_row = (d.width + kTile - 1) / kTile;
+    return d;
+}
+
+}  // namespace mact
+
+using namespace mact;
+
+extern "C" {
+
+void mact_config_default(mact_config *cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->rgb.gamma_threshold = 0.081;
+    cfg->rgb.gamma_slope = 4.5;
+    cfg->rgb.gamma_offset = 0.099;
+    cfg->rgb.gamma_exponent = 1.0 / 0.45;
+    const double m[9] = {0.412391, 0.357584, 0.180481, 0.212639, 0.715169, 0.072192, 0.019331, 0.119195, 0.950532};
+    std::memcpy(cfg->rgb.rgb_to_xyz, m, sizeof(m));
+    cfg->rgb.white[0] = 0.950456;
+    cfg->rgb.white[1] = 1.0;
+    cfg->rgb.white[2] = 1.089058;
+    cfg->exact = 0;
+    cfg->lab_n = 4;
+    cfg->lab_m = 4;
+    cfg->hsi_n = 5;
+    cfg->hsi_coeffs = 0;
+    cfg->sct_n = cfg->sct_m = cfg->sct_r = 5;
+}
+
+mact_status mact_create(const mact_config *cfg, mact_handle *out)
+{
+    if (!cfg || !out) return inval("mact_create: NULL argument");
+    if (cfg->exact != 0 && cfg->exact != 1) return inval("exact must be 0 or 1");
+    mact_ctx *h = new (std::nothrow) mact_ctx();
+    if (!h) return MACT_E_NOMEM;
+    h->cfg = *cfg;
+    mact_status st = build_coeffs(*cfg, h->co);
+    if (st != MACT_OK) { delete h; return st; }
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_gamma, 256 * sizeof(float));
+    if (e == cudaSuccess) {
+        float g[256];
+        build_gamma(cfg->rgb, g);
+        e = cudaMemcpy(h->d_gamma, g, sizeof(g), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_kernel, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        st = cuda_status(e, "mact_create");
+        mact_destroy(h);
+        return st;
+    }
+    *out = h;
+    return MACT_OK;
+}
+
+mact_status mact_destroy(mact_handle h)
+{
+    if (!h) return inval("mact_destroy: NULL handle");
+    cudaDeviceSynchronize();
+    if (h->d_gamma) cudaFree(h->d_gamma);
+    if (h->d_work) cudaFree(h->d_work);
+    if (h->h_work) cudaFreeHost(h->h_work);
+    if (h->ev_copy) cudaEventDestroy(h->ev_copy);
+    if (h->ev_kernel) cudaEventDestroy(h->ev_kernel);
+    delete h;
+    return MACT_OK;
+}
+
+mact_status mact_convert(mact_handle h, const mact_image *img, mact_stream stream)
+{
+    if (!h) return inval("mact_convert: NULL handle");
+    mact_status st = check_image(img);
+    if (st != MACT_OK) return st;
+    if (img->width == 0 || img->height == 0) return MACT_OK;
+    ImageDesc d = make_desc(*img);
+    return cuda_status(launch_convert(*h, d, (cudaStream_t)stream), "mact_convert launch");
+}
+
+mact_status mact_convert_batch(mact_handle h, const mact_image *imgs, int32_t count, mact_stream stream)
+{
+    if (!h) return inval("mact_convert_batch: NULL handle");
+    if (count < 0) return inval("negative image count");
+    if (count > 0 && !imgs) return inval("imgs is NULL");
+    for (int32_t i = 0; i < count; ++i) {
+        mact_status st = check_image(&imgs[i]);
+        if (st != MACT_OK) return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(h->batch_mu);
+    // the staging buffer and the device work list are reused: wait for the
+    // previous call's copy (host side) and kernel (stream side) first
+    cudaError_t e = cudaEventSynchronize(h->ev_copy);
+    if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch: previous copy");
+    if (count > h->work_cap) {
+        e = cudaEventSynchronize(h->ev_kernel);
+        if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch: previous kernel");
+        int64_t cap = count < 64 ? 64 : count;
+        if (h->d_work) cudaFree(h->d_work);
+        if (h->h_work) cudaFreeHost(h->h_work);
+        h->d_work = nullptr;
+        h->h_work = nullptr;
+        h->work_cap = 0;
+        e = cudaMalloc(&h->d_work, 256 + cap * sizeof(ImageDesc));
+        if (e == cudaSuccess) e = cudaMemset(h->d_work, 0, 256);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_work, cap * sizeof(ImageDesc));
+        if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch: work list allocation");
+        h->work_cap = cap;
+    }
+    int64_t total = 0;
+    int32_t n = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        if (imgs[i].width == 0 || imgs[i].height == 0) continue;
+        ImageDesc d = make_desc(imgs[i]);
+        d.tile_begin = total;
+        total += tiles_of(d);
+        h->h_work[n++] = d;
+    }
+    if (total == 0) return MACT_OK;
+    unsigned long long *d_ctr = reinterpret_cast<unsigned long long *>(h->d_work);
+    ImageDesc *d_imgs = reinterpret_cast<ImageDesc *>(reinterpret_cast<char *>(h->d_work) + 256);
+    e = cudaStreamWaitEvent(s, h->ev_kernel, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_imgs, h->h_work, n * sizeof(ImageDesc), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_copy, s);
+    if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch: work list copy");
+    if (h->batch_blocks_per_sm == 0) h->batch_blocks_per_sm = batch_blocks_per_sm(*h);
+    int64_t grid = (int64_t)h->num_sms * h->batch_blocks_per_sm;
+    if (grid > total) grid = total;
+    e = launch_batch(*h, d_imgs, n, total, d_ctr, (int)grid, s);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_kernel, s);
+    return cuda_status(e, "mact_convert_batch launch");
+}
+
+mact_status mact_lut_build(mact_handle h, int32_t n, float *d_lut, mact_stream stream)
+{
+    if (!h) return inval("mact_lut_build: NULL handle");
+    if (n < 2 || n > 64) return inval("LUT size must be 2..64");
+    if (!d_lut) return inval("d_lut is NULL");
+    return cuda_status(launch_lut_build(*h, n, d_lut, (cudaStream_t)stream), "mact_lut_build launch");
+}
+
+mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, int32_t n, const uint8_t *d_rgb,
+                            int64_t npix, float *const d_out[3], int32_t *d_sel, mact_stream stream)
+{
+    if (!h) return inval("mact_lut_interp: NULL handle");
+    if (method < MACT_TRILINEAR || method > MACT_TETRA) return inval("unknown interpolation method");
+    if (n < 2 || n > 64) return inval("LUT size must be 2..64");
+    if (npix < 0) return inval("negative pixel count");
+    if (npix == 0) return MACT_OK;
+    if (!d_lut || !d_rgb || !d_out || !d_out[0] || !d_out[1] || !d_out[2]) return inval("NULL pointer");
+    return cuda_status(launch_lut_interp(*h, method, d_lut, n, d_rgb, npix, d_out, d_sel, (cudaStream_t)stream),
+                       "mact_lut_interp launch");
+}
+
+const char *mact_strerror(mact_status st)
+{
+    switch (st) {
+    case MACT_OK: return "ok";
+    case MACT_E_INVAL: return "invalid argument";
+    case MACT_E_NOMEM: return "out of memory or admission budget";
+    case MACT_E_CUDA: return "CUDA error";
+    case MACT_E_UNSUPPORTED: return "unsupported";
+    case MACT_E_TIMEOUT: return "timed out";
+    case MACT_E_BUSY: return "busy";
+    }
+    return "unknown status";
+}
+
+const char *mact_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// common.cuh -- internal types and device helpers shared by the libmact
+// kernels.  Nothing here is exported; the public interface is include/mact.h.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mact.h"
+
+namespace mact {
+
+// Pixels per CTA tile of the streaming engine: 256 threads x 4 pixels.
+constexpr int kThreads = 256;
+constexpr int kPxPerThread = 4;
+constexpr int kTile = kThreads * kPxPerThread;      // 1024 pixels, 3072 input bytes
+constexpr int kTileVec = kTile * 3 / 16;            // 192 16-byte input vectors
+
+// Coefficients travel by value in the kernel parameter block, so every
+// uniform coefficient is a constant-bank operand of its FFMA.  Arrays are
+// ascending powers, zero-padded to the fixed evaluation degree (padding with
+// leading zeros leaves every Horner step bit-identical).
+struct Coeffs {
+    float m[9];          // rgb_to_xyz row c divided by white[c]
+    float lab_d[6];      // rational: p - q (degree 4); polynomial: p (degree 5)
+    float lab_q[5];      // rational: q (degree 4)
+    int32_t lab_rational;
+    float hsi[6];        // arctan(sqrt(3) x) on |x| <= 1, degree 5
+    float sct_p[6];      // 2 arcsin(y/sqrt 2), y = sqrt(1 - B/L), degree 5
+    float sct_q[6];      // arccos(x) on [0, 0.5], degree 5
+    float sct_f[6];      // arctan(x) on [0, 254/255], degree 5
+    float sct_g[6];      // pi/2 - arctan(w) on [1/255, 1], degree 5
+};
+
+// One image (or a contiguous run treated as one row) for the tile engine.
+struct ImageDesc {
+    const uint8_t *rgb;
+    void *out[3];
+    int64_t width;        // pixels per row (the whole image if contiguous)
+    int64_t height;       // rows
+    int64_t pitch;        // input row pitch in bytes
+    int64_t opitch;       // output row pitch in elements
+    int64_t tiles_per_row;
+    int64_t tile_begin;   // prefix sum of tiles over a batch
+    int32_t space;
+    int32_t dtype;
+};
+
+// Horner evaluation a0 + x (a1 + x (a2 + ...)) with FMA, degree D.
+template <int D>
+__device__ __forceinline__ float horner(const float *a, float x)
+{
+    float s = a[D];
+#pragma unroll
+    for (int i = D - 1; i >= 0; --i) s = fmaf(s, x, a[i]);
+    return s;
+}
+
+// Reciprocal: hardware approximation (rcp.approx.ftz.f32) refined by one
+// Newton-Raphson step r' = r + r (1 - q r) (the classical iteration for 1/q,
+// quadratic convergence).  Used only on arguments in [4e-4, 4].
+__device__ __forceinline__ float rcp_nr(float q)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
+    float e = fmaf(-q, r, 1.0f);
+    return fmaf(r, e, r);
+}
+
+// Fast quotient a / b via rcp.approx (about 2 ulp); used where the tolerance
+// allows it (HSI hue argument, saturation).
+__device__ __forceinline__ float div_approx(float a, float b)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+    return a * r;
+}
+
+// Streaming (evict-first) stores of 4 consecutive results.
+__device__ __forceinline__ void store4(float *p, float a, float b, float c, float d)
+{
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(a, b, c, d));
+}
+__device__ __forceinline__ void store4(__half *p, float a, float b, float c, float d)
+{
+    __half2 lo = __floats2half2_rn(a, b);
+    __half2 hi = __floats2half2_rn(c, d);
+    uint2 v;
+    v.x = *reinterpret_cast<uint32_t *>(&lo);
+    v.y = *reinterpret_cast<uint32_t *>(&hi);
+    __stcs(reinterpret_cast<uint2 *>(p), v);
+}
+__device__ __forceinline__ void store1(float *p, float a) { __stcs(p, a); }
+__device__ __forceinline__ void store1(__half *p, float a) { *p = __float2half_rn(a); }
+
+}  // namespace mact

@@ -1,0 +1,50 @@
+// internal.h -- host-side state of a libmact handle and the launchers each
+// kernel file provides.  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+
+struct mact_ctx {
+    int device = 0;
+    int num_sms = 0;
+    mact_config cfg{};
+    mact::Coeffs co{};
+    float *d_gamma = nullptr;            // 256 FP32 entries (Eq. equ_rgb_lin of each code)
+
+    // batched form: work list (image descriptors) and the tile counters
+    std::mutex batch_mu;
+    mact::ImageDesc *h_work = nullptr;   // pinned staging
+    void *d_work = nullptr;              // [2 x u64 counters][ImageDesc x cap]
+    int64_t work_cap = 0;
+    cudaEvent_t ev_copy = nullptr;       // staging copy finished
+    cudaEvent_t ev_kernel = nullptr;     // last batch kernel finished
+    int batch_blocks_per_sm = 0;
+};
+
+namespace mact {
+
+void set_error(const std::string &msg);
+mact_status cuda_status(cudaError_t e, const char *what);
+
+// k_convert.cu
+cudaError_t launch_convert(const mact_ctx &h, const ImageDesc &im, cudaStream_t s);
+cudaError_t launch_batch(const mact_ctx &h, const ImageDesc *d_imgs, int32_t count,
+                         int64_t total_tiles, unsigned long long *d_counters, int grid,
+                         cudaStream_t s);
+int batch_blocks_per_sm(const mact_ctx &h);
+
+// k_lut.cu
+cudaError_t launch_lut_build(const mact_ctx &h, int n, float *d_lut, cudaStream_t s);
+cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut, int n,
+                              const uint8_t *d_rgb, int64_t npix, float *const out[3],
+                              int32_t *d_sel, cudaStream_t s);
+
+// tile count of an image in the streaming engine
+int64_t tiles_of(const ImageDesc &im);
+
+}  // namespace mact

@@ -1,0 +1,229 @@
+"""Thin ctypes binding of libmact.so (include/mact.h).
+
+Argument marshalling only: every step of every transform runs in the CUDA
+kernels of libmact.so.  PyTorch supplies device memory (tensors) and streams;
+the functions below take torch tensors, pass their device pointers and sizes
+through the C ABI, and raise ``MactError`` on any non-zero status.  There is
+no CPU fallback: if the library cannot be loaded, every call raises.
+
+Names mirror the C entry points (``mact_create``, ``mact_convert``, ...).
+"""
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+SPACES = {"cielab": 0, "hsi": 1, "sct": 2}
+DTYPES = {torch.float32: 0, torch.float16: 1}
+METHODS = {"trilinear": 0, "prism": 1, "pyramid": 2, "tetra": 3}
+
+MACT_OK = 0
+
+
+class MactError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__("%s failed: status %d (%s)%s" % (
+            where, status, _lib_strerror(status), (": " + detail) if detail else ""))
+
+
+class RGBDef(ctypes.Structure):
+    _fields_ = [("gamma_threshold", ctypes.c_double), ("gamma_slope", ctypes.c_double),
+                ("gamma_offset", ctypes.c_double), ("gamma_exponent", ctypes.c_double),
+                ("rgb_to_xyz", ctypes.c_double * 9), ("white", ctypes.c_double * 3)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("rgb", RGBDef), ("exact", ctypes.c_int32), ("lab_n", ctypes.c_int32),
+                ("lab_m", ctypes.c_int32), ("hsi_n", ctypes.c_int32), ("hsi_coeffs", ctypes.c_int32),
+                ("sct_n", ctypes.c_int32), ("sct_m", ctypes.c_int32), ("sct_r", ctypes.c_int32)]
+
+
+class Image(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_void_p), ("width", ctypes.c_int64), ("height", ctypes.c_int64),
+                ("pitch_bytes", ctypes.c_int64), ("space", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("out", ctypes.c_void_p * 3), ("out_pitch_elems", ctypes.c_int64)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libmact.so (building it first if it is absent)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            _build.build()
+        L = ctypes.CDLL(path)
+        L.mact_config_default.argtypes = [ctypes.POINTER(Config)]
+        L.mact_config_default.restype = None
+        L.mact_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(_VP)]
+        L.mact_destroy.argtypes = [_VP]
+        L.mact_convert.argtypes = [_VP, ctypes.POINTER(Image), _VP]
+        L.mact_convert_batch.argtypes = [_VP, ctypes.POINTER(Image), ctypes.c_int32, _VP]
+        L.mact_lut_build.argtypes = [_VP, ctypes.c_int32, _VP, _VP]
+        L.mact_lut_interp.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32, _VP, ctypes.c_int64,
+                                      ctypes.POINTER(_VP * 3), _VP, _VP]
+        L.mact_strerror.argtypes = [ctypes.c_int]
+        L.mact_strerror.restype = ctypes.c_char_p
+        L.mact_last_error.argtypes = []
+        L.mact_last_error.restype = ctypes.c_char_p
+        for name in ("mact_create", "mact_destroy", "mact_convert", "mact_convert_batch",
+                     "mact_lut_build", "mact_lut_interp"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _lib_strerror(st):
+    try:
+        return lib().mact_strerror(st).decode()
+    except Exception:  # noqa: BLE001 - message formatting only
+        return "?"
+
+
+def _check(st, where):
+    if st != MACT_OK:
+        raise MactError(st, where, lib().mact_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return _VP(stream.cuda_stream)
+
+
+def mact_config_default(**overrides):
+    """The paper's defaults (BT.709, D65, CIELAB (4,4), HSI n=5 on [0,1],
+    SCT (5,5,5)); keyword overrides set top-level fields (exact, lab_n, ...)."""
+    cfg = Config()
+    lib().mact_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k in ("matrix", "rgb_to_xyz"):
+            for i, x in enumerate(v):
+                cfg.rgb.rgb_to_xyz[i] = x
+        elif k == "white":
+            for i, x in enumerate(v):
+                cfg.rgb.white[i] = x
+        elif k.startswith("gamma_"):
+            setattr(cfg.rgb, k, v)
+        else:
+            setattr(cfg, k, int(v))
+    return cfg
+
+
+class Handle:
+    """Owns a mact_handle; destroyed with the object."""
+
+    def __init__(self, ptr, cfg):
+        self.ptr = ptr
+        self.cfg = cfg
+
+    def close(self):
+        if self.ptr:
+            lib().mact_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+def mact_create(cfg=None, **overrides):
+    if cfg is None:
+        cfg = mact_config_default(**overrides)
+    h = _VP()
+    _check(lib().mact_create(ctypes.byref(cfg), ctypes.byref(h)), "mact_create")
+    return Handle(h, cfg)
+
+
+def _image(rgb, space, out):
+    if rgb.dtype != torch.uint8 or rgb.dim() != 3 or rgb.shape[2] != 3:
+        raise ValueError("rgb must be a (H, W, 3) uint8 tensor")
+    if rgb.stride(2) != 1 or rgb.stride(1) != 3:
+        raise ValueError("rgb pixels must be interleaved and rows dense (stride (pitch, 3, 1))")
+    if out.dim() != 3 or out.shape[0] != 3 or out.shape[1:] != rgb.shape[:2]:
+        raise ValueError("out must have shape (3, H, W)")
+    if out.stride(2) != 1:
+        raise ValueError("out rows must be dense")
+    H, W = rgb.shape[0], rgb.shape[1]
+    img = Image()
+    img.rgb = rgb.data_ptr()
+    img.width = W
+    img.height = H
+    img.pitch_bytes = rgb.stride(0)
+    img.space = SPACES[space] if isinstance(space, str) else int(space)
+    img.dtype = DTYPES[out.dtype]
+    for c in range(3):
+        img.out[c] = out[c].data_ptr()
+    img.out_pitch_elems = out.stride(1)
+    return img
+
+
+def mact_convert(h, rgb, space="cielab", dtype=torch.float32, out=None, stream=None):
+    """Convert one (H, W, 3) uint8 CUDA image; returns a (3, H, W) tensor."""
+    if out is None:
+        out = torch.empty((3, rgb.shape[0], rgb.shape[1]), dtype=dtype, device=rgb.device)
+    img = _image(rgb, space, out)
+    _check(lib().mact_convert(h.ptr, ctypes.byref(img), _stream(stream)), "mact_convert")
+    return out
+
+
+def mact_convert_batch(h, images, dtype=torch.float32, outs=None, stream=None):
+    """images: list of (rgb (H, W, 3) uint8 CUDA tensor, space); one launch.
+    Returns the list of (3, H, W) outputs."""
+    n = len(images)
+    if outs is None:
+        outs = [torch.empty((3, r.shape[0], r.shape[1]), dtype=dtype, device=r.device) for r, _ in images]
+    arr = (Image * max(n, 1))()
+    for i, ((rgb, space), out) in enumerate(zip(images, outs)):
+        arr[i] = _image(rgb, space, out)
+    _check(lib().mact_convert_batch(h.ptr, arr, n, _stream(stream)), "mact_convert_batch")
+    return outs
+
+
+def mact_lut_build(h, n, out=None, device="cuda", stream=None):
+    """n^3 x 3 FP32 LUT of the exact CIELAB at the lattice nodes."""
+    if out is None:
+        out = torch.empty((n, n, n, 3), dtype=torch.float32, device=device)
+    _check(lib().mact_lut_build(h.ptr, n, _VP(out.data_ptr()), _stream(stream)), "mact_lut_build")
+    return out
+
+
+def mact_lut_interp(h, method, lut, rgb, out=None, sel=False, stream=None):
+    """Interpolate the (npix, 3) or (H, W, 3) uint8 pixels of rgb in an
+    (n, n, n, 3) FP32 LUT.  Returns (3, npix) planes and, if sel, the int32
+    selection ids ((lower-corner node)*8 + simplex)."""
+    if lut.dtype != torch.float32 or not lut.is_contiguous() or lut.dim() != 4 or lut.shape[3] != 3:
+        raise ValueError("lut must be a contiguous (n, n, n, 3) float32 tensor")
+    if rgb.dtype != torch.uint8 or not rgb.is_contiguous() or rgb.shape[-1] != 3:
+        raise ValueError("rgb must be a contiguous (..., 3) uint8 tensor")
+    n = lut.shape[0]
+    npix = rgb.numel() // 3
+    if out is None:
+        out = torch.empty((3, npix), dtype=torch.float32, device=rgb.device)
+    ptrs = (_VP * 3)(*(out[c].data_ptr() for c in range(3)))
+    s = torch.empty(npix, dtype=torch.int32, device=rgb.device) if sel else None
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    _check(lib().mact_lut_interp(h.ptr, m, _VP(lut.data_ptr()), n, _VP(rgb.data_ptr()), npix,
+                                 ctypes.byref(ptrs), _VP(s.data_ptr() if s is not None else 0),
+                                 _stream(stream)), "mact_lut_interp")
+    return (out, s) if sel else out
+
+
+def mact_strerror(status):
+    return lib().mact_strerror(status).decode()
+
+
+def mact_last_error():
+    return lib().mact_last_error().decode()

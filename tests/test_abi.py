@@ -1,0 +1,82 @@
+"""The C ABI library loads and exports every entry point include/mact.h
+declares; argument validation that needs no GPU behaves as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "mact.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*?[\s\*]+(mact_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1009_0854_gb300 import mact
+    return mact.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["mact_create", "mact_destroy", "mact_convert", "mact_convert_batch", "mact_lut_build",
+              "mact_lut_interp", "mact_strerror", "mact_last_error", "mact_config_default"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for n in declared_functions():
+        assert hasattr(L, n), n
+
+
+def test_config_default_is_the_papers(L):
+    from paper_1009_0854_gb300 import mact
+    cfg = mact.mact_config_default()
+    assert (cfg.lab_n, cfg.lab_m, cfg.hsi_n, cfg.hsi_coeffs) == (4, 4, 5, 0)
+    assert (cfg.sct_n, cfg.sct_m, cfg.sct_r, cfg.exact) == (5, 5, 5, 0)
+    assert list(cfg.rgb.white) == [0.950456, 1.0, 1.089058]
+    assert list(cfg.rgb.rgb_to_xyz)[:3] == [0.412391, 0.357584, 0.180481]
+    assert cfg.rgb.gamma_threshold == 0.081 and cfg.rgb.gamma_slope == 4.5
+
+
+@pytest.mark.parametrize("field,value", [("lab_n", 5), ("lab_m", 1), ("hsi_n", 6), ("hsi_coeffs", 2),
+                                         ("sct_n", 3), ("sct_r", 6), ("exact", 2)])
+def test_create_rejects_bad_config_before_touching_the_gpu(L, field, value):
+    from paper_1009_0854_gb300 import mact
+    cfg = mact.mact_config_default(**{field: value})
+    h = ctypes.c_void_p()
+    assert L.mact_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+    assert h.value is None
+    assert L.mact_last_error()
+
+
+def test_create_rejects_white_above_reference(L):
+    from paper_1009_0854_gb300 import mact
+    cfg = mact.mact_config_default(white=[0.9, 1.0, 1.089058])
+    h = ctypes.c_void_p()
+    assert L.mact_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+
+
+def test_null_arguments(L):
+    from paper_1009_0854_gb300 import mact
+    assert L.mact_create(None, None) == -1
+    img = mact.Image()
+    assert L.mact_convert(None, ctypes.byref(img), None) == -1
+    assert L.mact_convert_batch(None, None, 0, None) == -1
+    assert L.mact_lut_build(None, 17, None, None) == -1
+    assert L.mact_destroy(None) == -1
+
+
+def test_strerror(L):
+    from paper_1009_0854_gb300 import mact
+    assert mact.mact_strerror(0) == "ok"
+    assert mact.mact_strerror(-1) == "invalid argument"
+    assert mact.mact_strerror(-2).startswith("out of memory")
+    assert mact.mact_strerror(-5) == "timed out"
