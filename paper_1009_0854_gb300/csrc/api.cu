@@ -98,7 +98,8 @@ static mact_status build_coeffs(const mact_config &cfg, Coeffs &co)
         double rowsum = 0.0;
         for (int j = 0; j < 3; ++j) {
             if (!std::isfinite(d.rgb_to_xyz[3 * c + j])) return inval("rgb_to_xyz must be finite");
-            co.m[3 * c + j] = (float)(d.rgb_to_xyz[3 * c + j] / d.white[c]);
+            co.m64[3 * c + j] = d.rgb_to_xyz[3 * c + j] / d.white[c];
+            co.m[3 * c + j] = (float)co.m64[3 * c + j];
             rowsum += d.rgb_to_xyz[3 * c + j];
         }
         // white (k = 1,1,1) must map to t <= 1: the cube-root fits live on [0.008856, 1]
@@ -111,7 +112,10 @@ static mact_status build_coeffs(const mact_config &cfg, Coeffs &co)
     // cube root
     if (cfg.lab_m == 0) {
         if (cfg.lab_n < 2 || cfg.lab_n > 5) return inval("lab_n must be 2..5 for the polynomial (lab_m = 0)");
-        for (int i = 0; i < 6; ++i) co.lab_d[i] = (float)kCbrtPoly[cfg.lab_n - 2][i];
+        for (int i = 0; i < 6; ++i) {
+            co.lab_d[i] = (float)kCbrtPoly[cfg.lab_n - 2][i];
+            co.lab_p64[i] = kCbrtPoly[cfg.lab_n - 2][i];
+        }
         co.lab_rational = 0;
     } else {
         const RatRow *row = nullptr;
@@ -152,14 +156,16 @@ static mact_status build_coeffs(const mact_config &cfg, Coeffs &co)
     return MACT_OK;
 }
 
-// Eq. equ_rgb_lin for the 256 codes, in double, rounded once to FP32.
-static void build_gamma(const mact_rgb_def &d, float *g)
+// Eq. equ_rgb_lin for the 256 codes, in double; g32 gets it rounded once to
+// FP32, g64 keeps it in FP64.
+static void build_gamma(const mact_rgb_def &d, float *g32, double *g64)
 {
     for (int v = 0; v < 256; ++v) {
         double kp = v / 255.0;
         double k = kp < d.gamma_threshold ? kp / d.gamma_slope
                                           : std::pow((kp + d.gamma_offset) / (1.0 + d.gamma_offset), d.gamma_exponent);
-        g[v] = (float)k;
+        g32[v] = (float)k;
+        g64[v] = k;
     }
 }
 
@@ -170,7 +176,9 @@ static mact_status check_image(const mact_image *img)
     if (img->space < MACT_CIELAB || img->space > MACT_SCT) return inval("unknown space");
     if (img->dtype != MACT_F32 && img->dtype != MACT_F16) return inval("unknown dtype");
     if (img->width == 0 || img->height == 0) return MACT_OK;
-    if (img->width > (int64_t(1) << 40) || img->height > (int64_t(1) << 40)) return inval("image too large");
+    // at most 2^42 pixels: tile indices stay below 2^31
+    if (img->width > (int64_t(1) << 42) || img->height > ((int64_t(1) << 42) / img->width))
+        return inval("image too large (more than 2^42 pixels)");
     if (!img->rgb || !img->out[0] || !img->out[1] || !img->out[2]) return inval("NULL image pointer");
     if (img->height > 1 && img->pitch_bytes < 3 * img->width) return inval("pitch_bytes < 3*width");
     if (img->height > 1 && img->out_pitch_elems < img->width) return inval("out_pitch_elems < width");
@@ -238,11 +246,11 @@ mact_status mact_create(const mact_config *cfg, mact_handle *out)
     if (st != MACT_OK) { delete h; return st; }
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-    if (e == cudaSuccess) e = cudaMalloc(&h->d_gamma, 256 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_gamma, 256 * (sizeof(float) + sizeof(double)));
     if (e == cudaSuccess) {
-        float g[256];
-        build_gamma(cfg->rgb, g);
-        e = cudaMemcpy(h->d_gamma, g, sizeof(g), cudaMemcpyHostToDevice);
+        struct { float g32[256]; double g64[256]; } tab;
+        build_gamma(cfg->rgb, tab.g32, tab.g64);
+        e = cudaMemcpy(h->d_gamma, &tab, sizeof(tab), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_kernel, cudaEventDisableTiming);
@@ -346,7 +354,7 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
     if (!h) return inval("mact_lut_interp: NULL handle");
     if (method < MACT_TRILINEAR || method > MACT_TETRA) return inval("unknown interpolation method");
     if (n < 2 || n > 64) return inval("LUT size must be 2..64");
-    if (npix < 0) return inval("negative pixel count");
+    if (npix < 0 || npix > (int64_t(1) << 42)) return inval("pixel count out of range");
     if (npix == 0) return MACT_OK;
     if (!d_lut || !d_rgb || !d_out || !d_out[0] || !d_out[1] || !d_out[2]) return inval("NULL pointer");
     return cuda_status(launch_lut_interp(*h, method, d_lut, n, d_rgb, npix, d_out, d_sel, (cudaStream_t)stream),

@@ -10,17 +10,19 @@
 
 namespace mact {
 
-// Pixels per CTA tile of the streaming engine: 256 threads x 4 pixels.
+// Streaming engine geometry: 256 threads per CTA, 4 pixels per thread per
+// sub-block, 4 sub-blocks per tile -> 4096 pixels (12 KB of input) per tile.
 constexpr int kThreads = 256;
 constexpr int kPxPerThread = 4;
-constexpr int kTile = kThreads * kPxPerThread;      // 1024 pixels, 3072 input bytes
-constexpr int kTileVec = kTile * 3 / 16;            // 192 16-byte input vectors
+constexpr int kTile = kThreads * kPxPerThread * 4;
 
 // Coefficients travel by value in the kernel parameter block, so every
 // uniform coefficient is a constant-bank operand of its FFMA.  Arrays are
 // ascending powers, zero-padded to the fixed evaluation degree (padding with
 // leading zeros leaves every Horner step bit-identical).
 struct Coeffs {
+    double m64[9];       // rgb_to_xyz / white in FP64 (polynomial cube-root path)
+    double lab_p64[6];   // polynomial cube root in FP64, degree 5 (zero-padded)
     float m[9];          // rgb_to_xyz row c divided by white[c]
     float lab_d[6];      // rational: p - q (degree 4); polynomial: p (degree 5)
     float lab_q[5];      // rational: q (degree 4)
@@ -68,12 +70,28 @@ __device__ __forceinline__ float rcp_nr(float q)
 }
 
 // Fast quotient a / b via rcp.approx (about 2 ulp); used where the tolerance
-// allows it (HSI hue argument, saturation).
-__device__ __forceinline__ float div_approx(float a, float b)
+// allows it (HSI hue argument, saturation; SCT ratios).
+__device__ __forceinline__ float rcp_approx(float b)
 {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
-    return a * r;
+    return r;
+}
+__device__ __forceinline__ float div_approx(float a, float b) { return a * rcp_approx(b); }
+
+// Hardware reciprocal square root and square root approximations
+// (rsqrt.approx / sqrt.approx, a few ulp): no special-case branches.
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 // Streaming (evict-first) stores of 4 consecutive results.

@@ -1,29 +1,37 @@
 // engine.cuh -- the streaming tile engine shared by the transform and LUT
 // kernels: interleaved uint8 RGB in, three planes (and optionally a
-// per-pixel int32) out, THREADS x 4 pixels per CTA tile.
+// per-pixel int32) out.
 //
-// Data path per tile (HBM-bound: 3 bytes read and 12 (FP32) or 6 (FP16)
-// bytes written per pixel, nothing reused):
-//   1. 3/4 of the threads each load one 16-byte vector of the tile's
-//      12*THREADS input bytes (coalesced, streaming cache hint) into shared
-//      memory;
-//   2. every thread de-interleaves 4 consecutive pixels from three 32-bit
-//      shared-memory words (stride 3 words across a warp: conflict-free) and
-//      applies the operator;
-//   3. every thread writes its 4 results per plane as one 16-byte (FP32) or
-//      8-byte (FP16) streaming store, so a warp writes 512 contiguous bytes.
-// Short tiles (image tail) and misaligned ones (pitched rows, odd pointers)
-// take a byte-wise load and per-pixel stores instead.
+// The work is HBM-bound by design (3 bytes read, 12 (FP32) or 6 (FP16) bytes
+// written per pixel, nothing reused), so the engine's job is to keep the
+// per-pixel instruction count low and the memory system busy:
+//   * a tile is THREADS x 16 pixels (12*THREADS input bytes); every thread
+//     loads exactly three 16-byte vectors of it (coalesced, streaming hint)
+//     and stages them in shared memory;
+//   * each thread then de-interleaves 4 consecutive pixels at a time from
+//     three 32-bit shared-memory words (stride 3 words across a warp: no bank
+//     conflicts), four times per tile, and writes each plane's 4 results as
+//     one 16-byte (FP32) or 8-byte (FP16) streaming store -- a warp writes
+//     512 contiguous bytes per store instruction;
+//   * for contiguous, aligned images the persistent loop prefetches the next
+//     tile into registers while it computes the current one, and computes
+//     tile addresses with one multiply (no per-tile division);
+//   * pitched rows, misaligned pointers and the final partial tile take a
+//     guarded path (byte loads, per-pixel stores) that gives identical values.
 #pragma once
 
 #include "common.cuh"
 
 namespace mact {
 
+constexpr int kSubBlocks = 4;                        // 4 pixels per thread per sub-block
+
 template <int THREADS>
 struct TileShape {
-    static constexpr int px = THREADS * kPxPerThread;
-    static constexpr int vecs = px * 3 / 16;
+    static constexpr int sub = THREADS * kPxPerThread;   // pixels per sub-block
+    static constexpr int px = sub * kSubBlocks;          // pixels per tile
+    static constexpr int vecs = px * 3 / 16;             // 16-byte input vectors per tile
+    static_assert(vecs == 3 * THREADS, "three input vectors per thread");
 };
 
 template <int THREADS>
@@ -34,65 +42,164 @@ __host__ __device__ inline int64_t tiles_of_t(const ImageDesc &im)
     return im.height * ((im.width + P - 1) / P);
 }
 
-// Process tile t of image im with operator op.  sbuf holds
-// TileShape<THREADS>::vecs uint4.  If SEL, op's integer result is written to
-// sel (same geometry as the output planes).  Ends with sbuf still in use by
-// other threads: the caller must __syncthreads() before reusing it.
+// An image is streamable when it is one contiguous row with every base
+// pointer aligned for the vector accesses.
+template <typename OutT, bool SEL>
+__device__ __forceinline__ bool streamable(const ImageDesc &im, const int32_t *sel)
+{
+    constexpr uintptr_t omask = sizeof(OutT) == 4 ? 15 : 7;
+    uintptr_t oa = reinterpret_cast<uintptr_t>(im.out[0]) | reinterpret_cast<uintptr_t>(im.out[1]) |
+                   reinterpret_cast<uintptr_t>(im.out[2]);
+    bool ok = im.height == 1 && ((reinterpret_cast<uintptr_t>(im.rgb) & 15) == 0) && ((oa & omask) == 0);
+    if (SEL) ok = ok && ((reinterpret_cast<uintptr_t>(sel) & 15) == 0);
+    return ok;
+}
+
+template <int THREADS>
+__device__ __forceinline__ void load_tile(uint4 (&v)[3], const uint8_t *in)
+{
+    const uint4 *p = reinterpret_cast<const uint4 *>(in) + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = __ldcs(p + k * THREADS);
+}
+
+template <int THREADS>
+__device__ __forceinline__ void stage_tile(uint4 *sbuf, const uint4 (&v)[3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sbuf[threadIdx.x + k * THREADS] = v[k];
+}
+
+// Apply op to the 4 pixels of sub-block s owned by this thread.
+template <int THREADS, class Op>
+__device__ __forceinline__ void apply4(const uint4 *sbuf, int s, const Op &op, float (&v)[3][4], int (&sl)[4])
+{
+    const uint32_t *sw = reinterpret_cast<const uint32_t *>(sbuf) + s * 3 * THREADS + 3 * threadIdx.x;
+    const uint32_t w0 = sw[0], w1 = sw[1], w2 = sw[2];
+    // bytes: w0 = r0 g0 b0 r1 | w1 = g1 b1 r2 g2 | w2 = b2 r3 g3 b3
+    sl[0] = op(w0 & 255u, (w0 >> 8) & 255u, (w0 >> 16) & 255u, v[0][0], v[1][0], v[2][0]);
+    sl[1] = op(w0 >> 24, w1 & 255u, (w1 >> 8) & 255u, v[0][1], v[1][1], v[2][1]);
+    sl[2] = op((w1 >> 16) & 255u, w1 >> 24, w2 & 255u, v[0][2], v[1][2], v[2][2]);
+    sl[3] = op((w2 >> 8) & 255u, (w2 >> 16) & 255u, w2 >> 24, v[0][3], v[1][3], v[2][3]);
+}
+
+// Full, aligned tile: sbuf holds its input; outputs start at o* (+ sel).
+template <int THREADS, typename OutT, bool SEL, class Op>
+__device__ __forceinline__ void compute_full(const uint4 *sbuf, const Op &op, OutT *o0, OutT *o1, OutT *o2,
+                                             int32_t *sel)
+{
+#pragma unroll
+    for (int s = 0; s < kSubBlocks; ++s) {
+        float v[3][4];
+        int sl[4];
+        apply4<THREADS>(sbuf, s, op, v, sl);
+        const int p = s * TileShape<THREADS>::sub + kPxPerThread * threadIdx.x;
+        store4(o0 + p, v[0][0], v[0][1], v[0][2], v[0][3]);
+        store4(o1 + p, v[1][0], v[1][1], v[1][2], v[1][3]);
+        store4(o2 + p, v[2][0], v[2][1], v[2][2], v[2][3]);
+        if (SEL) __stcs(reinterpret_cast<int4 *>(sel + p), make_int4(sl[0], sl[1], sl[2], sl[3]));
+    }
+}
+
+// Guarded tile of cnt <= px pixels at any alignment.  Ends with a barrier
+// already passed after the staging; the caller synchronises before reusing
+// sbuf.
+template <int THREADS, typename OutT, bool SEL, class Op>
+__device__ __forceinline__ void compute_guarded(uint4 *sbuf, const uint8_t *in, int cnt, const Op &op, OutT *o0,
+                                                OutT *o1, OutT *o2, int32_t *sel)
+{
+    uint8_t *sb = reinterpret_cast<uint8_t *>(sbuf);
+    for (int i = threadIdx.x; i < 3 * cnt; i += THREADS) sb[i] = in[i];
+    __syncthreads();
+    for (int s = 0; s < kSubBlocks; ++s) {
+        const int p = s * TileShape<THREADS>::sub + kPxPerThread * threadIdx.x;
+        if (p >= cnt) break;
+        float v[3][4];
+        int sl[4];
+        apply4<THREADS>(sbuf, s, op, v, sl);
+#pragma unroll
+        for (int j = 0; j < kPxPerThread; ++j) {
+            if (p + j < cnt) {
+                store1(o0 + p + j, v[0][j]);
+                store1(o1 + p + j, v[1][j]);
+                store1(o2 + p + j, v[2][j]);
+                if (SEL) sel[p + j] = sl[j];
+            }
+        }
+    }
+}
+
+// Tile t of image im (any geometry): the guarded or, when full and aligned,
+// the vector path.  The caller synchronises before reusing sbuf.
 template <int THREADS, typename OutT, bool SEL, class Op>
 __device__ __forceinline__ void process_tile(const ImageDesc &im, int64_t t, const Op &op, uint4 *sbuf,
                                              int32_t *sel)
 {
     constexpr int P = TileShape<THREADS>::px;
-    constexpr int V = TileShape<THREADS>::vecs;
-    const int tid = threadIdx.x;
-    const int64_t row = t / im.tiles_per_row;
-    const int64_t x0 = (t - row * im.tiles_per_row) * P;
+    const uint32_t tpr = (uint32_t)im.tiles_per_row;     // < 2^31 (checked on the host)
+    const uint32_t tt = (uint32_t)t;
+    const uint32_t row = tt / tpr;
+    const int64_t x0 = (int64_t)(tt - row * tpr) * P;
     const int64_t rem_px = im.width - x0;
     const int cnt = rem_px < P ? (int)rem_px : P;
-    const uint8_t *in = im.rgb + row * im.pitch + 3 * x0;
-    const int64_t off = row * im.opitch + x0;
+    const uint8_t *in = im.rgb + (int64_t)row * im.pitch + 3 * x0;
+    const int64_t off = (int64_t)row * im.opitch + x0;
     OutT *o0 = reinterpret_cast<OutT *>(im.out[0]) + off;
     OutT *o1 = reinterpret_cast<OutT *>(im.out[1]) + off;
     OutT *o2 = reinterpret_cast<OutT *>(im.out[2]) + off;
+    int32_t *sl = SEL ? sel + off : nullptr;
     constexpr uintptr_t omask = sizeof(OutT) == 4 ? 15 : 7;
     uintptr_t oa = reinterpret_cast<uintptr_t>(o0) | reinterpret_cast<uintptr_t>(o1) |
                    reinterpret_cast<uintptr_t>(o2);
-    if (SEL) oa |= reinterpret_cast<uintptr_t>(sel + off);
+    if (SEL) oa |= reinterpret_cast<uintptr_t>(sl);
     const bool fast = cnt == P && ((reinterpret_cast<uintptr_t>(in) & 15) == 0) && ((oa & omask) == 0);
     if (fast) {
-        if (tid < V) sbuf[tid] = __ldcs(reinterpret_cast<const uint4 *>(in) + tid);
+        uint4 v[3];
+        load_tile<THREADS>(v, in);
+        stage_tile<THREADS>(sbuf, v);
+        __syncthreads();
+        compute_full<THREADS, OutT, SEL>(sbuf, op, o0, o1, o2, sl);
     } else {
-        uint8_t *sb = reinterpret_cast<uint8_t *>(sbuf);
-        for (int i = tid; i < 3 * cnt; i += THREADS) sb[i] = in[i];
+        compute_guarded<THREADS, OutT, SEL>(sbuf, in, cnt, op, o0, o1, o2, sl);
     }
-    __syncthreads();
+}
 
-    const uint32_t *sw = reinterpret_cast<const uint32_t *>(sbuf) + 3 * tid;
-    const uint32_t w0 = sw[0], w1 = sw[1], w2 = sw[2];
-    // bytes: w0 = r0 g0 b0 r1 | w1 = g1 b1 r2 g2 | w2 = b2 r3 g3 b3
-    float v[3][4];
-    int s[4];
-    s[0] = op(w0 & 255u, (w0 >> 8) & 255u, (w0 >> 16) & 255u, v[0][0], v[1][0], v[2][0]);
-    s[1] = op(w0 >> 24, w1 & 255u, (w1 >> 8) & 255u, v[0][1], v[1][1], v[2][1]);
-    s[2] = op((w1 >> 16) & 255u, w1 >> 24, w2 & 255u, v[0][2], v[1][2], v[2][2]);
-    s[3] = op((w2 >> 8) & 255u, (w2 >> 16) & 255u, w2 >> 24, v[0][3], v[1][3], v[2][3]);
-
-    const int p0 = kPxPerThread * tid;
-    if (fast) {
-        store4(o0 + p0, v[0][0], v[0][1], v[0][2], v[0][3]);
-        store4(o1 + p0, v[1][0], v[1][1], v[1][2], v[1][3]);
-        store4(o2 + p0, v[2][0], v[2][1], v[2][2], v[2][3]);
-        if (SEL) __stcs(reinterpret_cast<int4 *>(sel + off + p0), make_int4(s[0], s[1], s[2], s[3]));
-    } else {
-#pragma unroll
-        for (int j = 0; j < kPxPerThread; ++j) {
-            if (p0 + j < cnt) {
-                store1(o0 + p0 + j, v[0][j]);
-                store1(o1 + p0 + j, v[1][j]);
-                store1(o2 + p0 + j, v[2][j]);
-                if (SEL) sel[off + p0 + j] = s[j];
-            }
+// Whole image, persistent CTA loop.  Streamable images run the prefetching
+// vector loop over their full tiles and hand the partial last tile to the
+// guarded path; everything else walks tiles through process_tile.
+template <int THREADS, typename OutT, bool SEL, class Op>
+__device__ __forceinline__ void run_image(const ImageDesc &im, int64_t ntiles, const Op &op, uint4 *sbuf,
+                                          int32_t *sel)
+{
+    constexpr int P = TileShape<THREADS>::px;
+    if (streamable<OutT, SEL>(im, sel)) {
+        const int64_t nfull = im.width / P;
+        OutT *b0 = reinterpret_cast<OutT *>(im.out[0]);
+        OutT *b1 = reinterpret_cast<OutT *>(im.out[1]);
+        OutT *b2 = reinterpret_cast<OutT *>(im.out[2]);
+        int64_t t = blockIdx.x;
+        uint4 v[3];
+        if (t < nfull) load_tile<THREADS>(v, im.rgb + 3 * P * t);
+        for (; t < nfull; t += gridDim.x) {
+            __syncthreads();                 // previous tile's readers are done
+            stage_tile<THREADS>(sbuf, v);
+            __syncthreads();
+            const int64_t tn = t + gridDim.x;
+            if (tn < nfull) load_tile<THREADS>(v, im.rgb + 3 * P * tn);   // in flight during compute
+            const int64_t o = P * t;
+            compute_full<THREADS, OutT, SEL>(sbuf, op, b0 + o, b1 + o, b2 + o, SEL ? sel + o : nullptr);
         }
+        if (nfull < ntiles && blockIdx.x == (unsigned)(nfull % gridDim.x)) {
+            __syncthreads();
+            const int64_t o = P * nfull;
+            compute_guarded<THREADS, OutT, SEL>(sbuf, im.rgb + 3 * o, (int)(im.width - o), op, b0 + o, b1 + o,
+                                                b2 + o, SEL ? sel + o : nullptr);
+        }
+        return;
+    }
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        __syncthreads();
+        process_tile<THREADS, OutT, SEL>(im, t, op, sbuf, sel);
     }
 }
 

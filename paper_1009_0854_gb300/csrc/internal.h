@@ -14,7 +14,7 @@ struct mact_ctx {
     int num_sms = 0;
     mact_config cfg{};
     mact::Coeffs co{};
-    float *d_gamma = nullptr;            // 256 FP32 entries (Eq. equ_rgb_lin of each code)
+    float *d_gamma = nullptr;            // 256 FP32 then 256 FP64 entries (Eq. equ_rgb_lin of each code)
 
     // batched form: work list (image descriptors) and the tile counters
     std::mutex batch_mu;

@@ -16,19 +16,26 @@ int64_t tiles_of(const ImageDesc &im) { return tiles_of_t<kThreads>(im); }
 
 using Shape = TileShape<kThreads>;
 
-template <class Op, typename OutT, bool GAMMA>
+// Linearisation table staged in shared memory: none (HSI, SCT), 256 FP32
+// entries, or 256 FP64 entries (polynomial cube-root variant).
+enum { kNoTable = 0, kTable32 = 1, kTable64 = 2 };
+
+__device__ __forceinline__ void load_table(int kind, const float *gamma, double *sg)
+{
+    if (kind == kTable32) reinterpret_cast<float *>(sg)[threadIdx.x] = gamma[threadIdx.x];
+    else if (kind == kTable64) sg[threadIdx.x] = reinterpret_cast<const double *>(gamma + 256)[threadIdx.x];
+}
+
+template <class Op, typename OutT, int TABLE>
 __global__ void __launch_bounds__(kThreads)
 k_image(const __grid_constant__ ImageDesc im, const __grid_constant__ Coeffs co,
         const float *__restrict__ gamma, int64_t ntiles)
 {
-    __shared__ float sgam[256];
+    __shared__ double sgam[256];
     __shared__ uint4 sbuf[Shape::vecs];
-    if (GAMMA) sgam[threadIdx.x] = gamma[threadIdx.x];
-    const Op op{GAMMA ? sgam : nullptr, co};
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        __syncthreads();
-        process_tile<kThreads, OutT, false>(im, t, op, sbuf, nullptr);
-    }
+    load_table(TABLE, gamma, sgam);
+    const Op op{reinterpret_cast<const float *>(sgam), co};
+    run_image<kThreads, OutT, false>(im, ntiles, op, sbuf, nullptr);
 }
 
 // HSI and SCT operators take no table; give them the same aggregate shape.
@@ -37,7 +44,7 @@ struct WithTable : Op {
     __device__ WithTable(const float *, const Coeffs &c) : Op{c} {}
 };
 
-template <class Op, typename OutT, bool GAMMA>
+template <class Op, typename OutT, int GAMMA>
 static cudaError_t launch_one(const mact_ctx &h, const ImageDesc &im, cudaStream_t s)
 {
     const int64_t nt = tiles_of(im);
@@ -62,15 +69,15 @@ static cudaError_t dispatch_space(const mact_ctx &h, const ImageDesc &im, cudaSt
     const bool rat = h.co.lab_rational != 0;
     switch (im.space) {
     case MACT_CIELAB:
-        if (exact) return launch_one<OpCielab<true, true>, OutT, true>(h, im, s);
-        if (rat) return launch_one<OpCielab<false, true>, OutT, true>(h, im, s);
-        return launch_one<OpCielab<false, false>, OutT, true>(h, im, s);
+        if (exact) return launch_one<OpCielab<true, true>, OutT, kTable32>(h, im, s);
+        if (rat) return launch_one<OpCielab<false, true>, OutT, kTable32>(h, im, s);
+        return launch_one<OpCielab<false, false>, OutT, kTable64>(h, im, s);
     case MACT_HSI:
-        if (exact) return launch_one<WithTable<OpHsi<true>>, OutT, false>(h, im, s);
-        return launch_one<WithTable<OpHsi<false>>, OutT, false>(h, im, s);
+        if (exact) return launch_one<WithTable<OpHsi<true>>, OutT, kNoTable>(h, im, s);
+        return launch_one<WithTable<OpHsi<false>>, OutT, kNoTable>(h, im, s);
     default:
-        if (exact) return launch_one<WithTable<OpSct<true>>, OutT, false>(h, im, s);
-        return launch_one<WithTable<OpSct<false>>, OutT, false>(h, im, s);
+        if (exact) return launch_one<WithTable<OpSct<true>>, OutT, kNoTable>(h, im, s);
+        return launch_one<WithTable<OpSct<false>>, OutT, kNoTable>(h, im, s);
     }
 }
 
@@ -104,11 +111,12 @@ k_batch(const ImageDesc *__restrict__ imgs, int32_t count, int64_t total,
         unsigned long long *__restrict__ ctr, const __grid_constant__ Coeffs co,
         const float *__restrict__ gamma)
 {
-    __shared__ float sgam[256];
+    __shared__ double sgam64[256];
     __shared__ uint4 sbuf[Shape::vecs];
     __shared__ long long s_tile;
     __shared__ int s_img;
-    sgam[threadIdx.x] = gamma[threadIdx.x];
+    load_table((!EXACT && !RAT) ? kTable64 : kTable32, gamma, sgam64);
+    const float *sgam = reinterpret_cast<const float *>(sgam64);
     for (;;) {
         __syncthreads();   // previous tile finished with sbuf / s_tile
         if (threadIdx.x == 0) {

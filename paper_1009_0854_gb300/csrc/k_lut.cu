@@ -187,10 +187,7 @@ k_lut_interp(const __grid_constant__ ImageDesc im, const float *__restrict__ lut
         op.lut.p = lut;
     }
     op.n = n;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        __syncthreads();
-        process_tile<THREADS, float, SEL>(im, t, op, sbuf, sel);
-    }
+    run_image<THREADS, float, SEL>(im, ntiles, op, sbuf, sel);
 }
 
 template <int THREADS, int METHOD, bool SMEM, bool SEL>

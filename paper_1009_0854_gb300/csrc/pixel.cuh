@@ -18,26 +18,35 @@ constexpr float kLinOffset = 16.0f / 116.0f;
 // ------------------------------------------------------------------ CIELAB
 // Eq. equ_rgb_lin (table lookup, as the paper suggests), Eq. equ_rgb_xyz with
 // the rows pre-divided by the white point, Eq. equ_xyz_lab with the cube root
-// replaced by the minimax rational of Table tab_cbrt_rat.
+// replaced by the minimax rational of Table tab_cbrt_rat.  The
+// linearisation table holds FP32 entries, or FP64 entries for the polynomial
+// (lab_m = 0) variant.
 //
 // FP32 form of the rational: f = 1 + d(t)/q(t) with d = p - q.  Identical to
 // p/q in exact arithmetic; near t = 1, where f ~ 1 and a*, b* amplify
 // absolute errors by 500 and 200, d is small and its rounding error scales
 // with it, so the worst a* error over the 2^24 colours drops from ~2.2e-4
 // (p/q) to ~1.2e-4.
-template <bool RATIONAL>
 __device__ __forceinline__ float f_mact(float t, const Coeffs &co)
 {
-    float fa;
-    if (RATIONAL) {
-        float d = horner<4>(co.lab_d, t);
-        float q = horner<4>(co.lab_q, t);
-        fa = fmaf(d, rcp_nr(q), 1.0f);
-    } else {
-        fa = horner<5>(co.lab_d, t);
-    }
+    float d = horner<4>(co.lab_d, t);
+    float q = horner<4>(co.lab_q, t);
+    float fa = fmaf(d, rcp_nr(q), 1.0f);
     float fl = fmaf(kLinSlope, t, kLinOffset);
     return t > kKnee ? fa : fl;
+}
+
+// The cube-root polynomials of Table tab_cbrt_poly (lab_m = 0) have slopes up
+// to ~4.4 at t = 1 (t^(1/3) has 1/3), so the FP32 rounding of t alone moves
+// a* by more than 2e-4.  That option (which the paper rejects for its error)
+// is evaluated in FP64: t from an FP64 linearisation table and matrix, then
+// the polynomial.
+__device__ __forceinline__ double f_mact_poly64(double t, const Coeffs &co)
+{
+    double s = co.lab_p64[5];
+#pragma unroll
+    for (int i = 4; i >= 0; --i) s = fma(s, t, co.lab_p64[i]);
+    return t > 0.008856 ? s : 7.787 * t + 16.0 / 116.0;
 }
 
 __device__ __forceinline__ float f_exact(float t)
@@ -53,6 +62,18 @@ struct OpCielab {
     __device__ __forceinline__ int operator()(uint32_t r, uint32_t g, uint32_t b, float &o0, float &o1,
                                               float &o2) const
     {
+        if (!EXACT && !RATIONAL) {
+            const double *g64 = reinterpret_cast<const double *>(gam);
+            const double k0 = g64[r], k1 = g64[g], k2 = g64[b];
+            const double *m = co.m64;
+            const double fx = f_mact_poly64(fma(m[2], k2, fma(m[1], k1, m[0] * k0)), co);
+            const double fy = f_mact_poly64(fma(m[5], k2, fma(m[4], k1, m[3] * k0)), co);
+            const double fz = f_mact_poly64(fma(m[8], k2, fma(m[7], k1, m[6] * k0)), co);
+            o0 = (float)(116.0 * fy - 16.0);
+            o1 = (float)(500.0 * (fx - fy));
+            o2 = (float)(200.0 * (fy - fz));
+            return 0;
+        }
         float k0 = gam[r], k1 = gam[g], k2 = gam[b];
         float tx = fmaf(co.m[2], k2, fmaf(co.m[1], k1, co.m[0] * k0));
         float ty = fmaf(co.m[5], k2, fmaf(co.m[4], k1, co.m[3] * k0));
@@ -61,7 +82,7 @@ struct OpCielab {
         if (EXACT) {
             fx = f_exact(tx); fy = f_exact(ty); fz = f_exact(tz);
         } else {
-            fx = f_mact<RATIONAL>(tx, co); fy = f_mact<RATIONAL>(ty, co); fz = f_mact<RATIONAL>(tz, co);
+            fx = f_mact(tx, co); fy = f_mact(ty, co); fz = f_mact(tz, co);
         }
         o0 = fmaf(116.0f, fy, -16.0f);
         o1 = 500.0f * (fx - fy);
@@ -100,7 +121,9 @@ struct OpHsi {
         o0 = zero ? 0.0f : h;
         int sum = R + G + B;
         int mn = min(R, min(G, B));
-        o1 = sum > 0 ? 1.0f - div_approx((float)(3 * mn), (float)sum) : 0.0f;
+        // S = 1 - 3 min / sum, formed as (sum - 3 min) / sum: the numerator is
+        // an exact integer, so grays give exactly 0
+        o1 = sum > 0 ? div_approx((float)(sum - 3 * mn), (float)sum) : 0.0f;
         o2 = (float)sum * (1.0f / 765.0f);
         return 0;
     }
@@ -130,21 +153,26 @@ struct OpSct {
             A = atan2f(sqrtf((float)rg2), (float)B);
             Bang = atan2f((float)G, (float)R);
         } else {
-            bool arcs = 3 * B * B >= rg2;
-            float Ls = fmaxf(L, 1.0f);
-            float x = __fdiv_rn((float)B, Ls);
-            float y = sqrtf(__fdiv_rn((float)rg2, Ls * (Ls + (float)B)));
-            float pa = horner<5>(co.sct_p, y);
-            float qa = horner<5>(co.sct_q, x);
+            // branch-free: hardware rsqrt / sqrt / rcp approximations (a few
+            // ulp, far inside the 1e-5 tolerance) and selects
+            const float s2f = (float)max(s2, 1);
+            const float rl = rsqrt_approx(s2f);          // 1/L
+            L = s2f * rl;
+            const bool arcs = 3 * B * B >= rg2;          // B/L >= 0.5, exactly
+            const float x = (float)B * rl;
+            const float y = sqrt_approx((float)rg2 * rcp_approx(L * (L + (float)B)));
+            const float pa = horner<5>(co.sct_p, y);
+            const float qa = horner<5>(co.sct_q, x);
             A = arcs ? pa : qa;
-            bool useF = G < R;
-            int nn = useF ? G : R, dd = useF ? R : G;
-            float w = __fdiv_rn((float)nn, (float)max(dd, 1));
+            const bool useF = G < R;
+            const int nn = useF ? G : R, dd = useF ? R : G;
+            const float w = (float)nn * rcp_approx((float)max(dd, 1));
             float c[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) c[i] = useF ? co.sct_f[i] : co.sct_g[i];
             Bang = horner<5>(c, w);
-            if (R == 0) Bang = (G > 0) ? kPi / 2.0f : 0.0f;
+            Bang = (R == 0) ? ((G > 0) ? kPi / 2.0f : 0.0f) : Bang;
+            L = (s2 == 0) ? 0.0f : L;
         }
         if (s2 == 0) { A = 0.0f; Bang = 0.0f; }
         o0 = L;

@@ -31,11 +31,11 @@ def oracle_lut(N):
 @pytest.mark.parametrize("N", [2, 9, 17, 33, 64])
 def test_lut_build_matches_oracle(h, N):
     """Packing on the GPU (FP64 then rounded) equals the oracle's FP32 LUT to
-    one FP32 ulp."""
+    one FP32 ulp (plus 1e-12 where the value is 0 up to cancellation)."""
     g = mact.mact_lut_build(h, N).cpu().numpy()
     ref = oracle_lut(N) if N != 64 else O.lut_build(64)
     d = np.abs(g.astype(np.float64) - ref.astype(np.float64))
-    assert np.all(d <= np.spacing(np.abs(ref)).astype(np.float64) + 1e-30)
+    assert np.all(d <= np.spacing(np.abs(ref)).astype(np.float64) + 1e-12)
 
 
 @pytest.mark.parametrize("method", METHODS)

@@ -7,7 +7,7 @@ import torch
 import oracle as O
 from oracle import tables
 from paper_1009_0854_gb300 import mact, synth
-from parity import check_space, oracle_planes
+from parity import LAB_TOL, check_space, oracle_planes
 
 pytestmark = pytest.mark.gpu
 
@@ -124,14 +124,16 @@ def test_empty_image_is_a_no_op(dev):
 
 
 def test_closed_forms_on_gpu(dev):
-    """White -> L = 116 R(1) - 16 with a* = b* = 0; grays -> a* = b* = 0 (the
-    three t values are equal); exact white -> (100, 0, 0)."""
+    """Grays have equal t values in exact arithmetic, so a* = b* = 0; in FP32
+    the three matrix rows round differently, so they are 0 to within the
+    parity tolerance (one FP32 ulp of f is 6e-5 in a*); exact white ->
+    (100, 0, 0); gray hue and saturation are exactly 0."""
     v = torch.arange(256, dtype=torch.uint8, device=dev)
     grays = torch.stack([v, v, v], dim=1).reshape(1, 256, 3)
     for exact in (0, 1):
         out = mact.mact_convert(handle(exact=exact), grays, "cielab")
         torch.cuda.synchronize()
-        assert out[1].abs().max().item() < 1e-5 and out[2].abs().max().item() < 1e-5
+        assert out[1].abs().max().item() <= LAB_TOL and out[2].abs().max().item() <= LAB_TOL
         if exact:
             assert abs(out[0, 0, 255].item() - 100.0) < 2e-4
         hsi = mact.mact_convert(handle(exact=exact), grays, "hsi")
