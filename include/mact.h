@@ -145,6 +145,25 @@ mact_status mact_convert(mact_handle h, const mact_image *img, mact_stream strea
 mact_status mact_convert_batch(mact_handle h, const mact_image *imgs, int32_t count,
                                mact_stream stream);
 
+/* Same result as mact_convert_batch, without any memory allocation.  The
+ * paper has no counterpart: this exists for callers that cannot allocate
+ * device or pinned memory at call time -- real-time or certified pipelines
+ * whose memory is fixed at start-up, plug-ins and host callbacks that must
+ * not enter the allocator, processes whose device memory is fully held by
+ * another framework's pool.  The work list (at most 1024 images; count above
+ * that returns MACT_E_INVAL) and the tile counters live in a fixed array of
+ * about 90 KB compiled into the library; every GPU that loads the library
+ * keeps it until the process exits.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device
+ * current, so make the first call on each device before any stream capture.
+ * Every call shares the one array: calls whose work overlaps on the GPU
+ * (different streams, or different handles, at the same time) race and must
+ * be serialised by the caller.  Calls from several host threads are
+ * serialised by the library.  Uploads the work list with cudaMemsetAsync and
+ * cudaMemcpyAsync on stream, then launches the batched kernel. */
+mact_status mact_convert_batch_static(mact_handle h, const mact_image *imgs, int32_t count,
+                                      mact_stream stream);
+
 /* Packing step of the LUT methods: fill d_lut (n^3 x 3 FP32, layout
  * d_lut[((i*n + j)*n + k)*3 + c], R outermost) with the exact CIELAB of the
  * node codes 255*(i,j,k)/(n-1), computed in FP32 with cbrtf.  2 <= n <= 64. */

@@ -169,7 +169,7 @@ static void build_gamma(const mact_rgb_def &d, float *g32, double *g64)
     }
 }
 
-static mact_status check_image(const mact_image *img)
+mact_status check_image(const mact_image *img)
 {
     if (!img) return inval("image is NULL");
     if (img->width < 0 || img->height < 0) return inval("negative image size");
@@ -185,7 +185,7 @@ static mact_status check_image(const mact_image *img)
     return MACT_OK;
 }
 
-static ImageDesc make_desc(const mact_image &img)
+ImageDesc make_desc(const mact_image &img)
 {
     ImageDesc d{};
     d.rgb = img.rgb;

@@ -47,4 +47,8 @@ cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut,
 // tile count of an image in the streaming engine
 int64_t tiles_of(const ImageDesc &im);
 
+// api.cu: argument validation of one image, and its engine descriptor
+mact_status check_image(const mact_image *img);
+ImageDesc make_desc(const mact_image &img);
+
 }  // namespace mact

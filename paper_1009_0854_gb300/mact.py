@@ -69,6 +69,7 @@ def lib():
         L.mact_destroy.argtypes = [_VP]
         L.mact_convert.argtypes = [_VP, ctypes.POINTER(Image), _VP]
         L.mact_convert_batch.argtypes = [_VP, ctypes.POINTER(Image), ctypes.c_int32, _VP]
+        L.mact_convert_batch_static.argtypes = [_VP, ctypes.POINTER(Image), ctypes.c_int32, _VP]
         L.mact_lut_build.argtypes = [_VP, ctypes.c_int32, _VP, _VP]
         L.mact_lut_interp.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32, _VP, ctypes.c_int64,
                                       ctypes.POINTER(_VP * 3), _VP, _VP]
@@ -76,7 +77,7 @@ def lib():
         L.mact_strerror.restype = ctypes.c_char_p
         L.mact_last_error.argtypes = []
         L.mact_last_error.restype = ctypes.c_char_p
-        for name in ("mact_create", "mact_destroy", "mact_convert", "mact_convert_batch",
+        for name in ("mact_create", "mact_destroy", "mact_convert", "mact_convert_batch", "mact_convert_batch_static",
                      "mact_lut_build", "mact_lut_interp"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -189,6 +190,20 @@ def mact_convert_batch(h, images, dtype=torch.float32, outs=None, stream=None):
     for i, ((rgb, space), out) in enumerate(zip(images, outs)):
         arr[i] = _image(rgb, space, out)
     _check(lib().mact_convert_batch(h.ptr, arr, n, _stream(stream)), "mact_convert_batch")
+    return outs
+
+
+def mact_convert_batch_static(h, images, dtype=torch.float32, outs=None, stream=None):
+    """As mact_convert_batch, through the entry point that allocates nothing
+    in the library (its work list lives in a fixed device array; at most 1024
+    images).  Output tensors are still created here unless outs is given."""
+    n = len(images)
+    if outs is None:
+        outs = [torch.empty((3, r.shape[0], r.shape[1]), dtype=dtype, device=r.device) for r, _ in images]
+    arr = (Image * max(n, 1))()
+    for i, ((rgb, space), out) in enumerate(zip(images, outs)):
+        arr[i] = _image(rgb, space, out)
+    _check(lib().mact_convert_batch_static(h.ptr, arr, n, _stream(stream)), "mact_convert_batch_static")
     return outs
 
 
