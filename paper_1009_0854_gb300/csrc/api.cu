@@ -254,6 +254,7 @@ mact_status mact_create(const mact_config *cfg, mact_handle *out)
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_kernel, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_lut, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         st = cuda_status(e, "mact_create");
         mact_destroy(h);
@@ -272,6 +273,8 @@ mact_status mact_destroy(mact_handle h)
     if (h->h_work) cudaFreeHost(h->h_work);
     if (h->ev_copy) cudaEventDestroy(h->ev_copy);
     if (h->ev_kernel) cudaEventDestroy(h->ev_kernel);
+    if (h->d_lut4) cudaFree(h->d_lut4);
+    if (h->ev_lut) cudaEventDestroy(h->ev_lut);
     delete h;
     return MACT_OK;
 }
@@ -357,8 +360,28 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
     if (npix < 0 || npix > (int64_t(1) << 42)) return inval("pixel count out of range");
     if (npix == 0) return MACT_OK;
     if (!d_lut || !d_rgb || !d_out || !d_out[0] || !d_out[1] || !d_out[2]) return inval("NULL pointer");
-    return cuda_status(launch_lut_interp(*h, method, d_lut, n, d_rgb, npix, d_out, d_sel, (cudaStream_t)stream),
-                       "mact_lut_interp launch");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!lut_needs_pack(n))
+        return cuda_status(launch_lut_interp(*h, method, d_lut, n, d_rgb, npix, d_out, d_sel, nullptr, s),
+                           "mact_lut_interp launch");
+    // large LUT: repack into the handle's float4 buffer, read by the kernel
+    std::lock_guard<std::mutex> lock(h->lut_mu);
+    const int64_t nodes = (int64_t)n * n * n;
+    cudaError_t e = cudaSuccess;
+    if (nodes > h->lut4_cap) {
+        e = cudaEventSynchronize(h->ev_lut);
+        if (e == cudaSuccess && h->d_lut4) e = cudaFree(h->d_lut4);
+        h->d_lut4 = nullptr;
+        h->lut4_cap = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_lut4, nodes * sizeof(float4));
+        if (e != cudaSuccess) return cuda_status(e, "mact_lut_interp: LUT buffer");
+        h->lut4_cap = nodes;
+    }
+    e = cudaStreamWaitEvent(s, h->ev_lut, 0);   // previous reader of the buffer (any stream)
+    if (e == cudaSuccess) e = launch_lut_pack4(d_lut, n, h->d_lut4, s);
+    if (e == cudaSuccess) e = launch_lut_interp(*h, method, d_lut, n, d_rgb, npix, d_out, d_sel, h->d_lut4, s);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_lut, s);
+    return cuda_status(e, "mact_lut_interp launch");
 }
 
 const char *mact_strerror(mact_status st)

@@ -24,6 +24,12 @@ struct mact_ctx {
     cudaEvent_t ev_copy = nullptr;       // staging copy finished
     cudaEvent_t ev_kernel = nullptr;     // last batch kernel finished
     int batch_blocks_per_sm = 0;
+
+    // LUT interpolation: float4 copy of a large LUT (n > 17), grown on demand
+    std::mutex lut_mu;
+    float4 *d_lut4 = nullptr;
+    int64_t lut4_cap = 0;                // nodes
+    cudaEvent_t ev_lut = nullptr;        // last interpolation kernel that read d_lut4
 };
 
 namespace mact {
@@ -42,7 +48,9 @@ int batch_blocks_per_sm(const mact_ctx &h);
 cudaError_t launch_lut_build(const mact_ctx &h, int n, float *d_lut, cudaStream_t s);
 cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut, int n,
                               const uint8_t *d_rgb, int64_t npix, float *const out[3],
-                              int32_t *d_sel, cudaStream_t s);
+                              int32_t *d_sel, const float4 *d_lut4, cudaStream_t s);
+cudaError_t launch_lut_pack4(const float *d_lut, int n, float4 *d_lut4, cudaStream_t s);
+bool lut_needs_pack(int n);
 
 // tile count of an image in the streaming engine
 int64_t tiles_of(const ImageDesc &im);

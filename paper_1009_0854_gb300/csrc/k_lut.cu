@@ -2,16 +2,21 @@
 // tetrahedral interpolators (Section "Comparison with 3D Lookup Table
 // Interpolation Methods"), on the streaming tile engine.
 //
-// Extraction is integer-only so that the cell and simplex chosen are
-// bit-identical to any exact implementation: along each axis
+// Extraction is bit-identical to an integer implementation: along each axis
 // s = v (n-1), idx = s div 255, rem = s mod 255, and the code v = 255 uses
-// idx = n-2, rem = 255; the fraction is rem/255.  Simplex choices compare the
-// integer remainders.
+// idx = n-2, rem = 255; the fraction is rem/255.  Every CTA tabulates, per
+// 8-bit code and axis, the node offset idx * stride and the fraction, so a
+// pixel's cell costs three shared loads; simplex choices compare fractions,
+// which order exactly as the integer remainders do (x -> x/255 is strictly
+// increasing on the integers 0..255 in FP32).
 //
 // LUT placement: for n <= 17 every CTA stages the whole LUT in shared memory
-// as float4 nodes (17^3 x 16 B = 78.6 KB), so each node is one 16-byte
-// shared load; larger LUTs (33^3 = 431 KB) stay in global memory, read
-// through the read-only path (they stay resident in L2 and partly in L1).
+// as float4 nodes (17^3 x 16 B = 78.6 KB), so a node is one 16-byte shared
+// load.  Larger LUTs (33^3: 575 KB as float4) are first repacked into float4
+// nodes in a scratch buffer of the handle (one small kernel per call) and
+// read from global memory (L1/L2 resident).  For n = 9, 17, 33 the node
+// strides are compile-time constants, so node addresses are immediate
+// offsets from the cell's base.
 #include "engine.cuh"
 #include "internal.h"
 
@@ -19,6 +24,11 @@ namespace mact {
 
 constexpr int kLutSmemMaxN = 17;
 constexpr int kLutThreadsSmem = 512;
+// Cell extraction: false = integer arithmetic per pixel (div by 255 as a
+// multiply-shift), true = per-code tables in shared memory.  The gathers of
+// the interpolation already saturate the shared/L1 data pipe, so the
+// arithmetic form (no extra shared loads) is the default.
+constexpr bool kLocateByTable = false;
 
 // --------------------------------------------------------------- packing
 
@@ -52,62 +62,88 @@ cudaError_t launch_lut_build(const mact_ctx &h, int n, float *d_lut, cudaStream_
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------- interpolation
-
-__device__ __forceinline__ void locate(uint32_t v, int n, int &idx, int &rem)
+// packed float3 nodes -> float4 nodes (the fourth lane unused)
+__global__ void k_lut_pack4(const float *__restrict__ lut, int nodes, float4 *__restrict__ out)
 {
-    const int s = (int)v * (n - 1);
-    idx = s / 255;
-    rem = s - 255 * idx;
-    if (idx == n - 1) { idx = n - 2; rem = 255; }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nodes) out[i] = make_float4(lut[3 * i], lut[3 * i + 1], lut[3 * i + 2], 0.0f);
 }
 
-// Node fetch from shared (float4) or global (packed float3) storage.
-template <bool SMEM>
-struct Nodes;
-template <>
-struct Nodes<true> {
-    const float4 *p;
-    __device__ __forceinline__ float4 operator[](int i) const { return p[i]; }
-};
-template <>
-struct Nodes<false> {
-    const float *p;
-    __device__ __forceinline__ float4 operator[](int i) const
-    {
-        return make_float4(__ldg(p + 3 * i), __ldg(p + 3 * i + 1), __ldg(p + 3 * i + 2), 0.0f);
-    }
+// ---------------------------------------------------------- interpolation
+
+// Per-code extraction table entry: node offset along the axis and fraction.
+struct AxisEntry {
+    int off;
+    float f;
 };
 
-__device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, 0.f); }
+__device__ __forceinline__ void fill_axis_tables(AxisEntry *tab, int n)
+{
+    // tab[axis * 256 + v], axis 0 = R (stride n^2), 1 = G (n), 2 = B (1)
+    for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) {
+        const int axis = i >> 8, v = i & 255;
+        const int s = v * (n - 1);
+        int idx = s / 255, rem = s - 255 * idx;
+        if (idx == n - 1) { idx = n - 2; rem = 255; }
+        const int stride = axis == 0 ? n * n : (axis == 1 ? n : 1);
+        tab[i].off = idx * stride;
+        tab[i].f = (float)rem / 255.0f;
+    }
+}
+
 __device__ __forceinline__ float4 f4sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, 0.f); }
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, 0.f); }
 __device__ __forceinline__ float4 f4fma(float4 a, float s, float4 c)
 {
     return make_float4(fmaf(a.x, s, c.x), fmaf(a.y, s, c.y), fmaf(a.z, s, c.z), 0.f);
 }
 
-template <int METHOD, bool SMEM>
-struct OpLut {
-    Nodes<SMEM> lut;
+// Node strides: compile-time for N > 0, runtime otherwise.
+template <int N>
+struct Strides {
     int n;
+    __device__ __forceinline__ int r() const { return N > 0 ? N * N : n * n; }
+    __device__ __forceinline__ int g() const { return N > 0 ? N : n; }
+};
+
+template <int METHOD, int N>
+struct OpLut {
+    const float4 *lut;        // shared or global float4 nodes
+    const AxisEntry *tab;     // shared extraction table
+    Strides<N> st;
+    __device__ __forceinline__ static void locate(uint32_t v, int n, int &idx, float &f)
+    {
+        const int s = (int)v * (n - 1);
+        idx = s / 255;
+        int rem = s - 255 * idx;
+        if (idx == n - 1) { idx = n - 2; rem = 255; }
+        f = (float)rem / 255.0f;
+    }
+
     __device__ __forceinline__ int operator()(uint32_t r, uint32_t g, uint32_t b, float &o0, float &o1,
                                               float &o2) const
     {
-        int ir, ig, ib, rr, rg, rb;
-        locate(r, n, ir, rr);
-        locate(g, n, ig, rg);
-        locate(b, n, ib, rb);
-        const float fr = (float)rr * (1.0f / 255.0f);
-        const float fg = (float)rg * (1.0f / 255.0f);
-        const float fb = (float)rb * (1.0f / 255.0f);
-        const int base = (ir * n + ig) * n + ib;
-        const int sR = n * n, sG = n, sB = 1;   // node strides
+        const int sR = st.r(), sG = st.g(), sB = 1;
+        int base;
+        float fr, fg, fb;
+        if (kLocateByTable) {
+            const AxisEntry er = tab[r], eg = tab[256 + g], eb = tab[512 + b];
+            base = er.off + eg.off + eb.off;
+            fr = er.f; fg = eg.f; fb = eb.f;
+        } else {
+            const int n = st.g();
+            int ir, ig, ib;
+            locate(r, n, ir, fr);
+            locate(g, n, ig, fg);
+            locate(b, n, ib, fb);
+            base = ir * sR + ig * sG + ib;
+        }
+        const float4 *c = lut + base;
         float4 v;
         int simplex;
         if (METHOD == MACT_TRILINEAR) {
-            const float4 c000 = lut[base], c001 = lut[base + sB], c010 = lut[base + sG],
-                         c011 = lut[base + sG + sB], c100 = lut[base + sR], c101 = lut[base + sR + sB],
-                         c110 = lut[base + sR + sG], c111 = lut[base + sR + sG + sB];
+            const float4 c000 = c[0], c001 = c[sB], c010 = c[sG], c011 = c[sG + sB], c100 = c[sR],
+                         c101 = c[sR + sB], c110 = c[sR + sG], c111 = c[sR + sG + sB];
             // repeated linear interpolation along B, then G, then R
             const float4 c00 = f4fma(f4sub(c001, c000), fb, c000);
             const float4 c01 = f4fma(f4sub(c011, c010), fb, c010);
@@ -119,13 +155,10 @@ struct OpLut {
             simplex = 0;
         } else if (METHOD == MACT_PRISM) {
             // prism axis R; triangle in the G-B face chosen by rem_G >= rem_B
-            const bool lo = rg >= rb;
-            const float4 c000 = lut[base], c100 = lut[base + sR];
-            const float4 c011 = lut[base + sG + sB], c111 = lut[base + sR + sG + sB];
-            const int oe = lo ? sG : sB;          // c010 or c001
-            const float4 ce0 = lut[base + oe], ce1 = lut[base + sR + oe];
-            // lo:  c000 + (c010-c000) fg + (c011-c010) fb + R-linear part
-            // !lo: c000 + (c011-c001) fg + (c001-c000) fb + R-linear part
+            const bool lo = fg >= fb;
+            const int oe = lo ? sG : sB;   // c010 or c001
+            const float4 c000 = c[0], c100 = c[sR], c011 = c[sG + sB], c111 = c[sR + sG + sB];
+            const float4 ce0 = c[oe], ce1 = c[sR + oe];
             const float fa = lo ? fg : fb, fc = lo ? fb : fg;
             const float4 t0 = f4fma(f4sub(c011, ce0), fc, f4fma(f4sub(ce0, c000), fa, c000));
             const float4 t1 = f4fma(f4sub(c111, ce1), fc, f4fma(f4sub(ce1, c100), fa, c100));
@@ -133,14 +166,13 @@ struct OpLut {
             simplex = lo ? 0 : 1;
         } else if (METHOD == MACT_PYRAMID) {
             // apex c111; base on the face of the smallest fraction (B, then G, then R)
-            int oX, oY, oA;
+            int oX, oY;
             float fX, fY, fZ;
-            if (rb <= rr && rb <= rg) { oX = sR; oY = sG; fX = fr; fY = fg; fZ = fb; simplex = 0; }
-            else if (rg <= rr && rg <= rb) { oX = sR; oY = sB; fX = fr; fY = fb; fZ = fg; simplex = 1; }
+            if (fb <= fr && fb <= fg) { oX = sR; oY = sG; fX = fr; fY = fg; fZ = fb; simplex = 0; }
+            else if (fg <= fr && fg <= fb) { oX = sR; oY = sB; fX = fr; fY = fb; fZ = fg; simplex = 1; }
             else { oX = sG; oY = sB; fX = fg; fY = fb; fZ = fr; simplex = 2; }
-            oA = oX + oY;
-            const float4 c000 = lut[base], c111 = lut[base + sR + sG + sB];
-            const float4 cX = lut[base + oX], cY = lut[base + oY], cA = lut[base + oA];
+            const float4 c000 = c[0], c111 = c[sR + sG + sB];
+            const float4 cX = c[oX], cY = c[oY], cA = c[oX + oY];
             // c000 + (c111-cA) fZ + (cX-c000) fX + (cY-c000) fY + (cA-cX-cY+c000) fX fY
             const float4 cross = f4add(f4sub(f4sub(cA, cX), cY), c000);
             float4 acc = f4fma(f4sub(c111, cA), fZ, c000);
@@ -151,14 +183,13 @@ struct OpLut {
             // tetrahedral: path from c000 along the axes in decreasing fraction
             int o1, o2;
             float f1, f2, f3;
-            if (rr >= rg && rg >= rb)      { o1 = sR; o2 = sR + sG; f1 = fr; f2 = fg; f3 = fb; simplex = 0; }
-            else if (rr >= rb && rb > rg)  { o1 = sR; o2 = sR + sB; f1 = fr; f2 = fb; f3 = fg; simplex = 1; }
-            else if (rb > rr && rr >= rg)  { o1 = sB; o2 = sR + sB; f1 = fb; f2 = fr; f3 = fg; simplex = 2; }
-            else if (rg > rr && rr >= rb)  { o1 = sG; o2 = sR + sG; f1 = fg; f2 = fr; f3 = fb; simplex = 3; }
-            else if (rg >= rb && rb > rr)  { o1 = sG; o2 = sG + sB; f1 = fg; f2 = fb; f3 = fr; simplex = 4; }
+            if (fr >= fg && fg >= fb)      { o1 = sR; o2 = sR + sG; f1 = fr; f2 = fg; f3 = fb; simplex = 0; }
+            else if (fr >= fb && fb > fg)  { o1 = sR; o2 = sR + sB; f1 = fr; f2 = fb; f3 = fg; simplex = 1; }
+            else if (fb > fr && fr >= fg)  { o1 = sB; o2 = sR + sB; f1 = fb; f2 = fr; f3 = fg; simplex = 2; }
+            else if (fg > fr && fr >= fb)  { o1 = sG; o2 = sR + sG; f1 = fg; f2 = fr; f3 = fb; simplex = 3; }
+            else if (fg >= fb && fb > fr)  { o1 = sG; o2 = sG + sB; f1 = fg; f2 = fb; f3 = fr; simplex = 4; }
             else                           { o1 = sB; o2 = sG + sB; f1 = fb; f2 = fg; f3 = fr; simplex = 5; }
-            const float4 c000 = lut[base], c1 = lut[base + o1], c2 = lut[base + o2],
-                         c111 = lut[base + sR + sG + sB];
+            const float4 c000 = c[0], c1 = c[o1], c2 = c[o2], c111 = c[sR + sG + sB];
             float4 acc = f4fma(f4sub(c1, c000), f1, c000);
             acc = f4fma(f4sub(c2, c1), f2, acc);
             v = f4fma(f4sub(c111, c2), f3, acc);
@@ -170,38 +201,45 @@ struct OpLut {
     }
 };
 
-template <int THREADS, int METHOD, bool SMEM, bool SEL>
-__global__ void __launch_bounds__(THREADS)
-k_lut_interp(const __grid_constant__ ImageDesc im, const float *__restrict__ lut, int n, int32_t *sel,
-             int64_t ntiles)
+// SMEM: stage the packed float3 LUT as float4 nodes in shared memory.
+// Otherwise lut4 is the float4 copy in global memory.
+template <int THREADS, int MINB, int METHOD, int N, bool SMEM, bool SEL>
+__global__ void __launch_bounds__(THREADS, MINB)
+k_lut_interp(const __grid_constant__ ImageDesc im, const float *__restrict__ lut, const float4 *__restrict__ lut4,
+             int n, int32_t *sel, int64_t ntiles)
 {
     extern __shared__ float4 slut[];
     __shared__ uint4 sbuf[TileShape<THREADS>::vecs];
-    OpLut<METHOD, SMEM> op;
+    __shared__ AxisEntry stab[kLocateByTable ? 3 * 256 : 1];
+    if (kLocateByTable) fill_axis_tables(stab, n);
+    OpLut<METHOD, N> op;
     if constexpr (SMEM) {
         const int nodes = n * n * n;
         for (int i = threadIdx.x; i < nodes; i += THREADS)
             slut[i] = make_float4(lut[3 * i], lut[3 * i + 1], lut[3 * i + 2], 0.0f);
-        op.lut.p = slut;
+        op.lut = slut;
     } else {
-        op.lut.p = lut;
+        op.lut = lut4;
     }
-    op.n = n;
+    op.tab = stab;
+    op.st.n = n;
     run_image<THREADS, float, SEL>(im, ntiles, op, sbuf, sel);
 }
 
-template <int THREADS, int METHOD, bool SMEM, bool SEL>
-static cudaError_t launch_interp(const mact_ctx &h, const ImageDesc &im, const float *lut, int n,
-                                 int32_t *sel, cudaStream_t s)
+template <int THREADS, int MINB, int METHOD, int N, bool SMEM, bool SEL>
+static cudaError_t launch_interp(const mact_ctx &h, const ImageDesc &im, const float *lut, const float4 *lut4,
+                                 int n, int32_t *sel, cudaStream_t s)
 {
     const int64_t nt = tiles_of_t<THREADS>(im);
     if (nt == 0) return cudaSuccess;
-    auto kern = k_lut_interp<THREADS, METHOD, SMEM, SEL>;
-    const size_t smem = SMEM ? (size_t)kLutSmemMaxN * kLutSmemMaxN * kLutSmemMaxN * sizeof(float4) : 0;
-    static int occ = 0;
+    auto kern = k_lut_interp<THREADS, MINB, METHOD, N, SMEM, SEL>;
+    const size_t smem = SMEM ? (size_t)n * n * n * sizeof(float4) : 0;
+    static int occ_cache[kLutSmemMaxN + 1] = {0};
+    int &occ = occ_cache[SMEM ? n : 0];
     if (occ == 0) {
         if (SMEM) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            const int maxs = kLutSmemMaxN * kLutSmemMaxN * kLutSmemMaxN * (int)sizeof(float4);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
             if (e != cudaSuccess) return e;
         }
         int o = 0;
@@ -210,24 +248,34 @@ static cudaError_t launch_interp(const mact_ctx &h, const ImageDesc &im, const f
     }
     const int64_t cap = (int64_t)h.num_sms * occ;
     const int64_t grid = nt < cap ? nt : cap;
-    kern<<<(unsigned)grid, THREADS, smem, s>>>(im, lut, n, sel, nt);
+    kern<<<(unsigned)grid, THREADS, smem, s>>>(im, lut, lut4, n, sel, nt);
     return cudaGetLastError();
 }
 
-template <int METHOD>
-static cudaError_t interp_method(const mact_ctx &h, const ImageDesc &im, const float *lut, int n,
-                                 int32_t *sel, cudaStream_t s)
+template <int METHOD, int N, bool SMEM>
+static cudaError_t launch_sel(const mact_ctx &h, const ImageDesc &im, const float *lut, const float4 *lut4, int n,
+                              int32_t *sel, cudaStream_t s)
 {
-    if (n <= kLutSmemMaxN) {
-        if (sel) return launch_interp<kLutThreadsSmem, METHOD, true, true>(h, im, lut, n, sel, s);
-        return launch_interp<kLutThreadsSmem, METHOD, true, false>(h, im, lut, n, sel, s);
-    }
-    if (sel) return launch_interp<kThreads, METHOD, false, true>(h, im, lut, n, sel, s);
-    return launch_interp<kThreads, METHOD, false, false>(h, im, lut, n, sel, s);
+    constexpr int T = SMEM ? kLutThreadsSmem : kThreads;
+    constexpr int MINB = SMEM ? 2 : 4;   // cap registers at 64 so 1024+ threads stay resident
+    if (sel) return launch_interp<T, MINB, METHOD, N, SMEM, true>(h, im, lut, lut4, n, sel, s);
+    return launch_interp<T, MINB, METHOD, N, SMEM, false>(h, im, lut, lut4, n, sel, s);
+}
+
+template <int METHOD>
+static cudaError_t interp_method(const mact_ctx &h, const ImageDesc &im, const float *lut, const float4 *lut4,
+                                 int n, int32_t *sel, cudaStream_t s)
+{
+    if (n == 9) return launch_sel<METHOD, 9, true>(h, im, lut, lut4, n, sel, s);
+    if (n == 17) return launch_sel<METHOD, 17, true>(h, im, lut, lut4, n, sel, s);
+    if (n == 33) return launch_sel<METHOD, 33, false>(h, im, lut, lut4, n, sel, s);
+    if (n <= kLutSmemMaxN) return launch_sel<METHOD, 0, true>(h, im, lut, lut4, n, sel, s);
+    return launch_sel<METHOD, 0, false>(h, im, lut, lut4, n, sel, s);
 }
 
 cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut, int n, const uint8_t *d_rgb,
-                              int64_t npix, float *const out[3], int32_t *d_sel, cudaStream_t s)
+                              int64_t npix, float *const out[3], int32_t *d_sel, const float4 *d_lut4,
+                              cudaStream_t s)
 {
     ImageDesc im{};
     im.rgb = d_rgb;
@@ -241,11 +289,20 @@ cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut,
     const int P = n <= kLutSmemMaxN ? TileShape<kLutThreadsSmem>::px : TileShape<kThreads>::px;
     im.tiles_per_row = (npix + P - 1) / P;
     switch (method) {
-    case MACT_TRILINEAR: return interp_method<MACT_TRILINEAR>(h, im, d_lut, n, d_sel, s);
-    case MACT_PRISM: return interp_method<MACT_PRISM>(h, im, d_lut, n, d_sel, s);
-    case MACT_PYRAMID: return interp_method<MACT_PYRAMID>(h, im, d_lut, n, d_sel, s);
-    default: return interp_method<MACT_TETRA>(h, im, d_lut, n, d_sel, s);
+    case MACT_TRILINEAR: return interp_method<MACT_TRILINEAR>(h, im, d_lut, d_lut4, n, d_sel, s);
+    case MACT_PRISM: return interp_method<MACT_PRISM>(h, im, d_lut, d_lut4, n, d_sel, s);
+    case MACT_PYRAMID: return interp_method<MACT_PYRAMID>(h, im, d_lut, d_lut4, n, d_sel, s);
+    default: return interp_method<MACT_TETRA>(h, im, d_lut, d_lut4, n, d_sel, s);
     }
 }
+
+cudaError_t launch_lut_pack4(const float *d_lut, int n, float4 *d_lut4, cudaStream_t s)
+{
+    const int nodes = n * n * n;
+    k_lut_pack4<<<(nodes + 255) / 256, 256, 0, s>>>(d_lut, nodes, d_lut4);
+    return cudaGetLastError();
+}
+
+bool lut_needs_pack(int n) { return n > kLutSmemMaxN; }
 
 }  // namespace mact
