@@ -183,6 +183,65 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
                             const uint8_t *d_rgb, int64_t npix, float *const d_out[3],
                             int32_t *d_sel, mact_stream stream);
 
+/* ---- served form -------------------------------------------------------
+ * A conversion server with continuous batching (the paper has no serving
+ * layer; its transforms are what each request runs).  One scheduler thread
+ * per server admits queued requests in arrival order while a slot is free
+ * and the staging arena (mem_budget_bytes of device memory, allocated once by
+ * mact_serve_create) has room for the request's staged input and output,
+ * converts every request admitted in one tick with one launch of the batched
+ * kernel (as mact_convert_batch), and copies results back, on three streams
+ * (H2D, compute, D2H) so the copies of one tick overlap the kernel of
+ * another.  Requests that arrive while others are on the GPU join the next
+ * tick.  The result of each request equals mact_convert of that image. */
+
+typedef struct {
+    int64_t completed;   /* requests finished successfully */
+    int64_t failed;      /* requests whose copies or launch failed */
+    int64_t batches;     /* batched launches issued */
+    int64_t queued;      /* waiting for admission now */
+    int64_t in_flight;   /* admitted, not yet retired */
+    int64_t pixels;      /* pixels of the completed requests */
+    double p50_ms, p99_ms, max_ms;  /* submit-to-completion latency of completed requests */
+    double gpix_per_s;   /* completed pixels / (last completion - first submit) */
+} mact_serve_stats_t;
+
+/* Create a server for handle h (on h's device).  max_slots bounds the number
+ * of admitted, unfinished requests (1..65536); mem_budget_bytes (>= 4096)
+ * bounds their staging memory.  Device-resident inputs and outputs take no
+ * budget. */
+mact_status mact_serve_create(mact_handle h, size_t mem_budget_bytes, int32_t max_slots, mact_server_t *out);
+
+/* Queue one image.  img->rgb and img->out[] may each be host memory (pinned
+ * is fastest; pageable works but its copies block the scheduler) or device
+ * memory; host images are staged through the arena.  The buffers must stay
+ * valid until the request is done.  Returns a ticket.  MACT_E_NOMEM if the
+ * request alone needs more staging than the whole budget; MACT_E_BUSY once
+ * the server is shutting down. */
+mact_status mact_serve_submit(mact_server_t srv, const mact_image *img, uint64_t *ticket);
+
+/* Non-blocking status: *done = 1 once the request has finished (its outputs
+ * are written), failed, or was cancelled; *latency_ms = submit to
+ * completion.  Returns MACT_E_CUDA for a failed request. */
+mact_status mact_serve_poll(mact_server_t srv, uint64_t ticket, int32_t *done, double *latency_ms);
+
+/* Block until the request is done or timeout_ms passes (MACT_E_TIMEOUT). */
+mact_status mact_serve_wait(mact_server_t srv, uint64_t ticket, double timeout_ms, double *latency_ms);
+
+/* Cancel a request that has not been admitted yet (MACT_E_BUSY once it has). */
+mact_status mact_serve_cancel(mact_server_t srv, uint64_t ticket);
+
+/* Forget a finished request's record (MACT_E_BUSY while it is pending). */
+mact_status mact_serve_release(mact_server_t srv, uint64_t ticket);
+
+/* Counters and latency percentiles over the requests completed so far. */
+mact_status mact_serve_stats(mact_server_t srv, mact_serve_stats_t *out);
+
+/* Stop accepting requests, wait up to timeout_ms for queued and in-flight
+ * requests to finish, cancel any still queued after that (MACT_E_TIMEOUT),
+ * wait for in-flight work, and free the server. */
+mact_status mact_serve_destroy(mact_server_t srv, double timeout_ms);
+
 /* Message for a status code (static storage). */
 const char *mact_strerror(mact_status st);
 

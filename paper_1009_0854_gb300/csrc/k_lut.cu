@@ -87,7 +87,7 @@ __device__ __forceinline__ void fill_axis_tables(AxisEntry *tab, int n)
         if (idx == n - 1) { idx = n - 2; rem = 255; }
         const int stride = axis == 0 ? n * n : (axis == 1 ? n : 1);
         tab[i].off = idx * stride;
-        tab[i].f = (float)rem / 255.0f;
+        tab[i].f = (float)rem * (1.0f / 255.0f);
     }
 }
 
@@ -98,6 +98,14 @@ __device__ __forceinline__ float4 f4fma(float4 a, float s, float4 c)
     return make_float4(fmaf(a.x, s, c.x), fmaf(a.y, s, c.y), fmaf(a.z, s, c.z), 0.f);
 }
 
+// Node fetch: shared memory, or the read-only global path.
+template <bool SMEM>
+__device__ __forceinline__ float4 node(const float4 *p)
+{
+    if constexpr (SMEM) return *p;
+    else return __ldg(p);
+}
+
 // Node strides: compile-time for N > 0, runtime otherwise.
 template <int N>
 struct Strides {
@@ -106,7 +114,7 @@ struct Strides {
     __device__ __forceinline__ int g() const { return N > 0 ? N : n; }
 };
 
-template <int METHOD, int N>
+template <int METHOD, int N, bool SMEM>
 struct OpLut {
     const float4 *lut;        // shared or global float4 nodes
     const AxisEntry *tab;     // shared extraction table
@@ -117,7 +125,9 @@ struct OpLut {
         idx = s / 255;
         int rem = s - 255 * idx;
         if (idx == n - 1) { idx = n - 2; rem = 255; }
-        f = (float)rem / 255.0f;
+        // rem * fl(1/255): strictly increasing in rem, so comparing fractions
+        // orders cells exactly as the integer remainders do
+        f = (float)rem * (1.0f / 255.0f);
     }
 
     __device__ __forceinline__ int operator()(uint32_t r, uint32_t g, uint32_t b, float &o0, float &o1,
@@ -138,12 +148,13 @@ struct OpLut {
             locate(b, n, ib, fb);
             base = ir * sR + ig * sG + ib;
         }
-        const float4 *c = lut + base;
+        const float4 *cb = lut + base;
+        auto c = [cb](int k) { return node<SMEM>(cb + k); };
         float4 v;
         int simplex;
         if (METHOD == MACT_TRILINEAR) {
-            const float4 c000 = c[0], c001 = c[sB], c010 = c[sG], c011 = c[sG + sB], c100 = c[sR],
-                         c101 = c[sR + sB], c110 = c[sR + sG], c111 = c[sR + sG + sB];
+            const float4 c000 = c(0), c001 = c(sB), c010 = c(sG), c011 = c(sG + sB), c100 = c(sR),
+                         c101 = c(sR + sB), c110 = c(sR + sG), c111 = c(sR + sG + sB);
             // repeated linear interpolation along B, then G, then R
             const float4 c00 = f4fma(f4sub(c001, c000), fb, c000);
             const float4 c01 = f4fma(f4sub(c011, c010), fb, c010);
@@ -157,8 +168,8 @@ struct OpLut {
             // prism axis R; triangle in the G-B face chosen by rem_G >= rem_B
             const bool lo = fg >= fb;
             const int oe = lo ? sG : sB;   // c010 or c001
-            const float4 c000 = c[0], c100 = c[sR], c011 = c[sG + sB], c111 = c[sR + sG + sB];
-            const float4 ce0 = c[oe], ce1 = c[sR + oe];
+            const float4 c000 = c(0), c100 = c(sR), c011 = c(sG + sB), c111 = c(sR + sG + sB);
+            const float4 ce0 = c(oe), ce1 = c(sR + oe);
             const float fa = lo ? fg : fb, fc = lo ? fb : fg;
             const float4 t0 = f4fma(f4sub(c011, ce0), fc, f4fma(f4sub(ce0, c000), fa, c000));
             const float4 t1 = f4fma(f4sub(c111, ce1), fc, f4fma(f4sub(ce1, c100), fa, c100));
@@ -171,8 +182,8 @@ struct OpLut {
             if (fb <= fr && fb <= fg) { oX = sR; oY = sG; fX = fr; fY = fg; fZ = fb; simplex = 0; }
             else if (fg <= fr && fg <= fb) { oX = sR; oY = sB; fX = fr; fY = fb; fZ = fg; simplex = 1; }
             else { oX = sG; oY = sB; fX = fg; fY = fb; fZ = fr; simplex = 2; }
-            const float4 c000 = c[0], c111 = c[sR + sG + sB];
-            const float4 cX = c[oX], cY = c[oY], cA = c[oX + oY];
+            const float4 c000 = c(0), c111 = c(sR + sG + sB);
+            const float4 cX = c(oX), cY = c(oY), cA = c(oX + oY);
             // c000 + (c111-cA) fZ + (cX-c000) fX + (cY-c000) fY + (cA-cX-cY+c000) fX fY
             const float4 cross = f4add(f4sub(f4sub(cA, cX), cY), c000);
             float4 acc = f4fma(f4sub(c111, cA), fZ, c000);
@@ -189,7 +200,7 @@ struct OpLut {
             else if (fg > fr && fr >= fb)  { o1 = sG; o2 = sR + sG; f1 = fg; f2 = fr; f3 = fb; simplex = 3; }
             else if (fg >= fb && fb > fr)  { o1 = sG; o2 = sG + sB; f1 = fg; f2 = fb; f3 = fr; simplex = 4; }
             else                           { o1 = sB; o2 = sG + sB; f1 = fb; f2 = fg; f3 = fr; simplex = 5; }
-            const float4 c000 = c[0], c1 = c[o1], c2 = c[o2], c111 = c[sR + sG + sB];
+            const float4 c000 = c(0), c1 = c(o1), c2 = c(o2), c111 = c(sR + sG + sB);
             float4 acc = f4fma(f4sub(c1, c000), f1, c000);
             acc = f4fma(f4sub(c2, c1), f2, acc);
             v = f4fma(f4sub(c111, c2), f3, acc);
@@ -212,7 +223,7 @@ k_lut_interp(const __grid_constant__ ImageDesc im, const float *__restrict__ lut
     __shared__ uint4 sbuf[TileShape<THREADS>::vecs];
     __shared__ AxisEntry stab[kLocateByTable ? 3 * 256 : 1];
     if (kLocateByTable) fill_axis_tables(stab, n);
-    OpLut<METHOD, N> op;
+    OpLut<METHOD, N, SMEM> op;
     if constexpr (SMEM) {
         const int nodes = n * n * n;
         for (int i = threadIdx.x; i < nodes; i += THREADS)

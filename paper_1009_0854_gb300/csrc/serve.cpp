@@ -1,0 +1,483 @@
+// serve.cpp -- the served form: a conversion server with continuous
+// batching over one GPU.
+//
+// Requests (one image each, host or device buffers, any space and dtype)
+// are queued by mact_serve_submit.  One scheduler thread repeats a tick:
+//   1. admit queued requests in arrival order while a slot is free and the
+//      device staging arena (the memory budget, allocated once at create)
+//      has room for the request's staged input and output;
+//   2. for the requests admitted in this tick: copy host inputs to their
+//      staging on the H2D stream, then -- on the compute stream, after
+//      those copies -- convert all of them with ONE launch of the batched
+//      work-list kernel, then copy host outputs back on the D2H stream;
+//   3. retire requests whose completion event has fired (latency = submit
+//      to completion seen by the scheduler), release their slot and arena
+//      range.
+// Requests that arrive while earlier ones are on the GPU are admitted in the
+// next tick, so copies of one batch overlap the kernel of another
+// (iteration-level continuous batching).  Nothing waits on the device
+// without a bound: the scheduler polls events; mact_serve_wait and
+// mact_serve_destroy take timeouts.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace mact {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point a, Clock::time_point b)
+{
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+enum ReqState { kQueued = 0, kInFlight = 1, kDone = 2, kFailed = 3, kCancelled = 4 };
+
+struct Request {
+    uint64_t ticket = 0;
+    mact_image img{};          // as submitted
+    bool in_host = false, out_host = false;
+    size_t in_bytes = 0, out_bytes = 0, elem = 4;
+    size_t off = 0, len = 0;   // arena range
+    uint8_t *d_in = nullptr;
+    void *d_out[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_done = nullptr;
+    Clock::time_point t_submit, t_done;
+    int state = kQueued;
+    int64_t pixels = 0;
+};
+
+// First-fit allocator over [0, size) in 256-byte units.
+class Arena {
+public:
+    void reset(size_t size)
+    {
+        free_.clear();
+        free_[0] = size;
+        size_ = size;
+    }
+    bool alloc(size_t len, size_t *off)
+    {
+        len = (len + 255) & ~size_t(255);
+        if (len == 0) { *off = 0; return true; }
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= len) {
+                *off = it->first;
+                size_t rest = it->second - len, start = it->first + len;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t len)
+    {
+        len = (len + 255) & ~size_t(255);
+        if (len == 0) return;
+        auto it = free_.emplace(off, len).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+private:
+    std::map<size_t, size_t> free_;
+    size_t size_ = 0;
+};
+
+bool is_host_pointer(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear: unknown pointers are pageable host memory
+        return true;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+}  // namespace
+
+}  // namespace mact
+
+using namespace mact;
+
+struct mact_server {
+    mact_handle h = nullptr;
+    int device = 0;
+    size_t budget = 0;
+    int max_slots = 0;
+    void *arena_base = nullptr;
+    Arena arena;
+    cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
+
+    std::mutex mu;
+    std::condition_variable cv_work;     // submit -> scheduler
+    std::condition_variable cv_done;     // scheduler -> waiters
+    std::deque<Request *> queue;
+    std::vector<Request *> inflight;
+    std::map<uint64_t, Request *> reqs;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+
+    // statistics over retired requests
+    std::vector<double> latencies;
+    int64_t pixels_done = 0, batches = 0, failed = 0;
+    Clock::time_point t_first, t_last;
+    bool any_done = false;
+};
+
+namespace mact {
+
+static void fail_locked(mact_server *s, Request *r, const char *what, cudaError_t e)
+{
+    (void)what;
+    (void)e;
+    r->state = kFailed;
+    r->t_done = Clock::now();
+    s->failed++;
+}
+
+// One scheduler tick: admit, launch, retire.  Returns true if it did work.
+static bool serve_tick(mact_server *s)
+{
+    std::vector<Request *> batch;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        while (!s->queue.empty() && (int)s->inflight.size() + (int)batch.size() < s->max_slots) {
+            Request *r = s->queue.front();
+            size_t off = 0;
+            if (!s->arena.alloc(r->in_bytes + r->out_bytes, &off)) break;   // FIFO: wait for room
+            s->queue.pop_front();
+            r->off = off;
+            r->len = r->in_bytes + r->out_bytes;
+            r->state = kInFlight;
+            batch.push_back(r);
+        }
+    }
+    bool worked = !batch.empty();
+    if (worked) {
+        // stage pointers and H2D copies
+        std::vector<mact_image> imgs;
+        imgs.reserve(batch.size());
+        cudaError_t e = cudaSuccess;
+        for (Request *r : batch) {
+            uint8_t *base = static_cast<uint8_t *>(s->arena_base) + r->off;
+            mact_image im = r->img;
+            const int64_t W = im.width, H = im.height;
+            if (r->in_host) {
+                r->d_in = base;
+                const size_t sp = H == 1 ? (size_t)(3 * W) : (size_t)im.pitch_bytes;   // one row: pitch unused
+                if (e == cudaSuccess)
+                    e = cudaMemcpy2DAsync(r->d_in, 3 * W, im.rgb, sp, 3 * W, H, cudaMemcpyHostToDevice, s->s_h2d);
+                im.rgb = r->d_in;
+                im.pitch_bytes = 3 * W;
+            }
+            if (r->out_host) {
+                uint8_t *ob = base + ((r->in_bytes + 255) & ~size_t(255));
+                for (int c = 0; c < 3; ++c) {
+                    r->d_out[c] = ob + (size_t)c * W * H * r->elem;
+                    im.out[c] = r->d_out[c];
+                }
+                im.out_pitch_elems = W;
+            }
+            imgs.push_back(im);
+        }
+        cudaEvent_t ev_in = nullptr, ev_comp = nullptr;
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_comp, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in, s->s_h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->s_comp, ev_in, 0);
+        mact_status st = MACT_OK;
+        if (e == cudaSuccess) st = mact_convert_batch(s->h, imgs.data(), (int32_t)imgs.size(), s->s_comp);
+        if (e == cudaSuccess && st == MACT_OK) e = cudaEventRecord(ev_comp, s->s_comp);
+        if (e == cudaSuccess && st == MACT_OK) e = cudaStreamWaitEvent(s->s_d2h, ev_comp, 0);
+        for (Request *r : batch) {
+            if (e != cudaSuccess || st != MACT_OK) break;
+            const mact_image &im = r->img;
+            const int64_t W = im.width, H = im.height;
+            if (r->out_host) {
+                const size_t dp = H == 1 ? (size_t)W * r->elem : (size_t)im.out_pitch_elems * r->elem;
+                for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+                    e = cudaMemcpy2DAsync(im.out[c], dp, r->d_out[c], W * r->elem, W * r->elem, H,
+                                          cudaMemcpyDeviceToHost, s->s_d2h);
+            }
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_done, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(r->ev_done, s->s_d2h);
+        }
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_comp) cudaEventDestroy(ev_comp);
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->batches++;
+        for (Request *r : batch) {
+            if (e != cudaSuccess || st != MACT_OK || !r->ev_done) {
+                fail_locked(s, r, "serve", e);
+                s->arena.release(r->off, r->len);
+                if (e != cudaSuccess) set_error(std::string("mact_serve: ") + cudaGetErrorString(e));
+            } else {
+                s->inflight.push_back(r);
+            }
+        }
+        if (e != cudaSuccess || st != MACT_OK) s->cv_done.notify_all();
+    }
+    // retire
+    std::unique_lock<std::mutex> lk(s->mu);
+    bool retired = false;
+    for (size_t i = 0; i < s->inflight.size();) {
+        Request *r = s->inflight[i];
+        cudaError_t q = cudaEventQuery(r->ev_done);
+        if (q == cudaErrorNotReady) { ++i; continue; }
+        r->t_done = Clock::now();
+        if (q == cudaSuccess) {
+            r->state = kDone;
+            s->latencies.push_back(ms_since(r->t_submit, r->t_done));
+            s->pixels_done += r->pixels;
+            if (!s->any_done) { s->t_first = r->t_submit; s->any_done = true; }
+            s->t_last = r->t_done;
+        } else {
+            fail_locked(s, r, "serve", q);
+        }
+        cudaEventDestroy(r->ev_done);
+        r->ev_done = nullptr;
+        s->arena.release(r->off, r->len);
+        s->inflight[i] = s->inflight.back();
+        s->inflight.pop_back();
+        retired = true;
+    }
+    if (retired) s->cv_done.notify_all();
+    return worked || retired;
+}
+
+static void serve_loop(mact_server *s)
+{
+    cudaSetDevice(s->device);
+    for (;;) {
+        bool worked = serve_tick(s);
+        std::unique_lock<std::mutex> lk(s->mu);
+        if (s->stop && s->queue.empty() && s->inflight.empty()) break;
+        if (!worked) {
+            if (s->inflight.empty() && s->queue.empty())
+                s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+            else
+                s->cv_work.wait_for(lk, std::chrono::microseconds(20));   // poll completions
+        }
+    }
+}
+
+}  // namespace mact
+
+extern "C" {
+
+mact_status mact_serve_create(mact_handle h, size_t mem_budget_bytes, int32_t max_slots, mact_server_t *out)
+{
+    if (!h || !out) { set_error("mact_serve_create: NULL argument"); return MACT_E_INVAL; }
+    if (max_slots < 1 || max_slots > 65536) { set_error("max_slots must be 1..65536"); return MACT_E_INVAL; }
+    if (mem_budget_bytes < 4096) { set_error("mem_budget_bytes must be at least 4096"); return MACT_E_INVAL; }
+    mact_server *s = new (std::nothrow) mact_server();
+    if (!s) return MACT_E_NOMEM;
+    s->h = h;
+    s->device = h->device;
+    s->budget = mem_budget_bytes & ~size_t(255);
+    s->max_slots = max_slots;
+    cudaError_t e = cudaSetDevice(s->device);
+    if (e == cudaSuccess) e = cudaMalloc(&s->arena_base, s->budget);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_d2h, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        mact_status st = cuda_status(e, "mact_serve_create");
+        if (s->arena_base) cudaFree(s->arena_base);
+        if (s->s_h2d) cudaStreamDestroy(s->s_h2d);
+        if (s->s_comp) cudaStreamDestroy(s->s_comp);
+        if (s->s_d2h) cudaStreamDestroy(s->s_d2h);
+        delete s;
+        return st;
+    }
+    s->arena.reset(s->budget);
+    s->worker = std::thread(serve_loop, s);
+    *out = s;
+    return MACT_OK;
+}
+
+mact_status mact_serve_submit(mact_server_t s, const mact_image *img, uint64_t *ticket)
+{
+    if (!s || !img || !ticket) { set_error("mact_serve_submit: NULL argument"); return MACT_E_INVAL; }
+    mact_status st = check_image(img);
+    if (st != MACT_OK) return st;
+    Request *r = new (std::nothrow) Request();
+    if (!r) return MACT_E_NOMEM;
+    r->img = *img;
+    r->elem = img->dtype == MACT_F16 ? 2 : 4;
+    r->pixels = img->width * img->height;
+    if (r->pixels > 0) {
+        r->in_host = is_host_pointer(img->rgb);
+        r->out_host = is_host_pointer(img->out[0]);
+        if (r->out_host != is_host_pointer(img->out[1]) || r->out_host != is_host_pointer(img->out[2])) {
+            delete r;
+            set_error("mact_serve_submit: output planes must all be on the host or all on the device");
+            return MACT_E_INVAL;
+        }
+    }
+    r->in_bytes = r->in_host ? (size_t)(3 * r->pixels) : 0;
+    r->out_bytes = r->out_host ? (size_t)(3 * r->pixels) * r->elem : 0;
+    const size_t need = ((r->in_bytes + 255) & ~size_t(255)) + ((r->out_bytes + 255) & ~size_t(255));
+    if (need > s->budget) {
+        delete r;
+        set_error("mact_serve_submit: request needs more staging memory than the server's budget");
+        return MACT_E_NOMEM;
+    }
+    r->in_bytes = (r->in_bytes + 255) & ~size_t(255);
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) { delete r; set_error("mact_serve_submit: server is shutting down"); return MACT_E_BUSY; }
+        r->ticket = s->next_ticket++;
+        s->reqs[r->ticket] = r;
+        if (r->pixels == 0) {
+            r->state = kDone;
+            r->t_done = r->t_submit;
+        } else {
+            s->queue.push_back(r);
+        }
+        *ticket = r->ticket;
+    }
+    s->cv_work.notify_one();
+    return MACT_OK;
+}
+
+mact_status mact_serve_poll(mact_server_t s, uint64_t ticket, int32_t *done, double *latency_ms)
+{
+    if (!s || !done) { set_error("mact_serve_poll: NULL argument"); return MACT_E_INVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) { set_error("mact_serve_poll: unknown ticket"); return MACT_E_INVAL; }
+    Request *r = it->second;
+    *done = (r->state == kDone || r->state == kFailed || r->state == kCancelled) ? 1 : 0;
+    if (latency_ms) *latency_ms = *done ? ms_since(r->t_submit, r->t_done) : 0.0;
+    if (r->state == kFailed) return MACT_E_CUDA;
+    return MACT_OK;
+}
+
+mact_status mact_serve_wait(mact_server_t s, uint64_t ticket, double timeout_ms, double *latency_ms)
+{
+    if (!s) { set_error("mact_serve_wait: NULL server"); return MACT_E_INVAL; }
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) { set_error("mact_serve_wait: unknown ticket"); return MACT_E_INVAL; }
+    Request *r = it->second;
+    auto pred = [r] { return r->state == kDone || r->state == kFailed || r->state == kCancelled; };
+    if (!s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), pred)) {
+        set_error("mact_serve_wait: timed out");
+        return MACT_E_TIMEOUT;
+    }
+    if (latency_ms) *latency_ms = ms_since(r->t_submit, r->t_done);
+    return r->state == kFailed ? MACT_E_CUDA : MACT_OK;
+}
+
+mact_status mact_serve_cancel(mact_server_t s, uint64_t ticket)
+{
+    if (!s) { set_error("mact_serve_cancel: NULL server"); return MACT_E_INVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) { set_error("mact_serve_cancel: unknown ticket"); return MACT_E_INVAL; }
+    Request *r = it->second;
+    if (r->state != kQueued) { set_error("mact_serve_cancel: request already admitted"); return MACT_E_BUSY; }
+    s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+    r->state = kCancelled;
+    r->t_done = Clock::now();
+    s->cv_done.notify_all();
+    return MACT_OK;
+}
+
+mact_status mact_serve_release(mact_server_t s, uint64_t ticket)
+{
+    if (!s) { set_error("mact_serve_release: NULL server"); return MACT_E_INVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) { set_error("mact_serve_release: unknown ticket"); return MACT_E_INVAL; }
+    Request *r = it->second;
+    if (r->state == kQueued || r->state == kInFlight) { set_error("mact_serve_release: request pending"); return MACT_E_BUSY; }
+    s->reqs.erase(it);
+    delete r;
+    return MACT_OK;
+}
+
+mact_status mact_serve_stats(mact_server_t s, mact_serve_stats_t *out)
+{
+    if (!s || !out) { set_error("mact_serve_stats: NULL argument"); return MACT_E_INVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    std::vector<double> l = s->latencies;
+    out->completed = (int64_t)l.size();
+    out->failed = s->failed;
+    out->batches = s->batches;
+    out->queued = (int64_t)s->queue.size();
+    out->in_flight = (int64_t)s->inflight.size();
+    out->pixels = s->pixels_done;
+    if (!l.empty()) {
+        std::sort(l.begin(), l.end());
+        auto pct = [&l](double p) {
+            size_t k = (size_t)std::min<double>(l.size() - 1, std::max(0.0, p * (l.size() - 1) + 0.5));
+            return l[k];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+        out->max_ms = l.back();
+        const double span = ms_since(s->t_first, s->t_last);
+        out->gpix_per_s = span > 0 ? (double)s->pixels_done / (span * 1e-3) / 1e9 : 0.0;
+    }
+    return MACT_OK;
+}
+
+mact_status mact_serve_destroy(mact_server_t s, double timeout_ms)
+{
+    if (!s) { set_error("mact_serve_destroy: NULL server"); return MACT_E_INVAL; }
+    mact_status st = MACT_OK;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->cv_work.notify_all();
+        // bounded drain: everything queued or in flight must finish in time
+        if (!s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms),
+                                 [s] { return s->queue.empty() && s->inflight.empty(); })) {
+            // cancel what was never admitted; in-flight work still completes
+            for (Request *r : s->queue) { r->state = kCancelled; r->t_done = Clock::now(); }
+            s->queue.clear();
+            st = MACT_E_TIMEOUT;
+            set_error("mact_serve_destroy: drain timed out; queued requests cancelled");
+        }
+    }
+    s->cv_work.notify_all();
+    s->worker.join();   // the loop ends once in-flight work has retired
+    cudaStreamSynchronize(s->s_h2d);
+    cudaStreamSynchronize(s->s_comp);
+    cudaStreamSynchronize(s->s_d2h);
+    cudaStreamDestroy(s->s_h2d);
+    cudaStreamDestroy(s->s_comp);
+    cudaStreamDestroy(s->s_d2h);
+    cudaFree(s->arena_base);
+    for (auto &kv : s->reqs) delete kv.second;
+    delete s;
+    return st;
+}
+
+}  // extern "C"

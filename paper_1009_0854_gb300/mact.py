@@ -47,6 +47,16 @@ class Image(ctypes.Structure):
                 ("out", ctypes.c_void_p * 3), ("out_pitch_elems", ctypes.c_int64)]
 
 
+class ServeStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64), ("pixels", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("gpix_per_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib = None
 _VP = ctypes.c_void_p
 
@@ -73,6 +83,18 @@ def lib():
         L.mact_lut_build.argtypes = [_VP, ctypes.c_int32, _VP, _VP]
         L.mact_lut_interp.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32, _VP, ctypes.c_int64,
                                       ctypes.POINTER(_VP * 3), _VP, _VP]
+        L.mact_serve_create.argtypes = [_VP, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(_VP)]
+        L.mact_serve_submit.argtypes = [_VP, ctypes.POINTER(Image), ctypes.POINTER(ctypes.c_uint64)]
+        L.mact_serve_poll.argtypes = [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_double)]
+        L.mact_serve_wait.argtypes = [_VP, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+        L.mact_serve_cancel.argtypes = [_VP, ctypes.c_uint64]
+        L.mact_serve_release.argtypes = [_VP, ctypes.c_uint64]
+        L.mact_serve_stats.argtypes = [_VP, ctypes.POINTER(ServeStats)]
+        L.mact_serve_destroy.argtypes = [_VP, ctypes.c_double]
+        for name in ("mact_serve_create", "mact_serve_submit", "mact_serve_poll", "mact_serve_wait",
+                     "mact_serve_cancel", "mact_serve_release", "mact_serve_stats", "mact_serve_destroy"):
+            getattr(L, name).restype = ctypes.c_int
         L.mact_strerror.argtypes = [ctypes.c_int]
         L.mact_strerror.restype = ctypes.c_char_p
         L.mact_last_error.argtypes = []
@@ -234,6 +256,84 @@ def mact_lut_interp(h, method, lut, rgb, out=None, sel=False, stream=None):
                                  ctypes.byref(ptrs), _VP(s.data_ptr() if s is not None else 0),
                                  _stream(stream)), "mact_lut_interp")
     return (out, s) if sel else out
+
+
+# ------------------------------------------------------------- served form
+
+class Server:
+    """Owns a mact_server_t (continuous-batching conversion server)."""
+
+    def __init__(self, ptr, handle):
+        self.ptr = ptr
+        self.handle = handle      # keep the handle alive as long as the server
+        self._keep = {}           # ticket -> tensors referenced by the request
+
+    def close(self, timeout_ms=60000.0):
+        if self.ptr:
+            st = lib().mact_serve_destroy(self.ptr, timeout_ms)
+            self.ptr = None
+            self._keep.clear()
+            return st
+        return MACT_OK
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+def mact_serve_create(h, mem_budget_bytes, max_slots=64):
+    p = _VP()
+    _check(lib().mact_serve_create(h.ptr, int(mem_budget_bytes), int(max_slots), ctypes.byref(p)),
+           "mact_serve_create")
+    return Server(p, h)
+
+
+def mact_serve_submit(srv, rgb, space="cielab", out=None, dtype=torch.float32):
+    """Queue one (H, W, 3) uint8 image; rgb and out may be host (pinned or
+    pageable) or CUDA tensors.  Returns (ticket, out)."""
+    if out is None:
+        out = torch.empty((3, rgb.shape[0], rgb.shape[1]), dtype=dtype, device=rgb.device,
+                          pin_memory=(rgb.device.type == "cpu"))
+    img = _image(rgb, space, out)
+    t = ctypes.c_uint64()
+    _check(lib().mact_serve_submit(srv.ptr, ctypes.byref(img), ctypes.byref(t)), "mact_serve_submit")
+    srv._keep[t.value] = (rgb, out)
+    return t.value, out
+
+
+def mact_serve_poll(srv, ticket):
+    """(done, latency_ms); raises MactError for a failed request."""
+    d = ctypes.c_int32()
+    lat = ctypes.c_double()
+    _check(lib().mact_serve_poll(srv.ptr, ticket, ctypes.byref(d), ctypes.byref(lat)), "mact_serve_poll")
+    return bool(d.value), lat.value
+
+
+def mact_serve_wait(srv, ticket, timeout_ms=60000.0):
+    lat = ctypes.c_double()
+    _check(lib().mact_serve_wait(srv.ptr, ticket, float(timeout_ms), ctypes.byref(lat)), "mact_serve_wait")
+    return lat.value
+
+
+def mact_serve_cancel(srv, ticket):
+    _check(lib().mact_serve_cancel(srv.ptr, ticket), "mact_serve_cancel")
+
+
+def mact_serve_release(srv, ticket):
+    _check(lib().mact_serve_release(srv.ptr, ticket), "mact_serve_release")
+    srv._keep.pop(ticket, None)
+
+
+def mact_serve_stats(srv):
+    st = ServeStats()
+    _check(lib().mact_serve_stats(srv.ptr, ctypes.byref(st)), "mact_serve_stats")
+    return st.as_dict()
+
+
+def mact_serve_destroy(srv, timeout_ms=60000.0):
+    return srv.close(timeout_ms)
 
 
 def mact_strerror(status):
