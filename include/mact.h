@@ -183,6 +183,35 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
                             const uint8_t *d_rgb, int64_t npix, float *const d_out[3],
                             int32_t *d_sel, mact_stream stream);
 
+/* ---- differentiable RGB -> CIELAB ----------------------------------------
+ * Input d_x is LINEAR RGB (the output of Eq. equ_rgb_lin, e.g. a network's
+ * activations) as planar FP32 of shape (nbatch, 3, hw): plane c of image b
+ * starts at d_x + (b*3 + c)*hw.  Lab uses Eq. equ_rgb_xyz and equ_xyz_lab
+ * with the handle's cube-root rational (or cbrtf when created with exact = 1);
+ * the backward differentiates exactly what the forward evaluates, including
+ * the linear segment (slope 7.787) for t <= 0.008856.  Handles using the
+ * cube-root polynomials (lab_m = 0) return MACT_E_UNSUPPORTED.  At most
+ * 2^32 - 1 pixels per call.  Fastest when hw % 4 == 0 and every pointer is
+ * 16-byte aligned. */
+
+/* d_lab (nbatch, 3, hw) = CIELAB of d_x. */
+mact_status mact_lab_forward(mact_handle h, const float *d_x, int64_t nbatch, int64_t hw, float *d_lab,
+                             mact_stream stream);
+
+/* d_grad_x = J(d_x)^T d_grad_lab: the vector-Jacobian product of the
+ * forward at d_x (recomputed, nothing saved), shapes (nbatch, 3, hw). */
+mact_status mact_lab_backward(mact_handle h, const float *d_x, const float *d_grad_lab, int64_t nbatch,
+                              int64_t hw, float *d_grad_x, mact_stream stream);
+
+/* Fused forward + loss + backward: *d_loss (one device float) = mean over
+ * pixels of Delta E*ab (Eq. equ_cielab_dist) between Lab(d_x) and
+ * d_target_lab (nbatch, 3, hw); if d_grad_x is not NULL it receives
+ * dLoss/dx (0 where Delta E = 0).  The mean is reduced in a fixed order
+ * (deterministic).  Uses a small per-handle partial-sum buffer; calls on one
+ * handle are ordered by the library. */
+mact_status mact_lab_delta_e_loss(mact_handle h, const float *d_x, const float *d_target_lab, int64_t nbatch,
+                                  int64_t hw, float *d_loss, float *d_grad_x, mact_stream stream);
+
 /* ---- served form -------------------------------------------------------
  * A conversion server with continuous batching (the paper has no serving
  * layer; its transforms are what each request runs).  One scheduler thread

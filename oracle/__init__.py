@@ -77,6 +77,11 @@ def lib():
         L.orc_cube_eps_hsi.argtypes = [_D, ctypes.c_int, _D]
         L.orc_cube_eps_sct.argtypes = [ctypes.POINTER(RGBDef), ctypes.POINTER(SCTCoeffs), _D]
         L.orc_cube_eps_lut.argtypes = [ctypes.POINTER(RGBDef), ctypes.c_int, _F, ctypes.c_int, _D]
+        L.orc_lab_linear.argtypes = [ctypes.POINTER(RGBDef), ctypes.c_int, _D, ctypes.c_int, _D, ctypes.c_int,
+                                     _D, ctypes.c_int64, ctypes.c_int64, _D]
+        L.orc_lab_loss_grad.argtypes = [ctypes.POINTER(RGBDef), ctypes.c_int, _D, ctypes.c_int, _D, ctypes.c_int,
+                                        _D, _D, ctypes.c_int64, ctypes.c_int64, _D]
+        L.orc_lab_loss_grad.restype = ctypes.c_double
         L.orc_max_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -285,3 +290,34 @@ def cube_eps_lut(method, lut, rgbdef=None):
     out = (ctypes.c_double * 2)()
     lib().orc_cube_eps_lut(ctypes.byref(d), md, _ptr(lut, _F), lut.shape[0], out)
     return list(out)
+
+
+# --------------------------------------------- differentiable RGB -> CIELAB
+
+def _lab_args(exact, n, m):
+    p, q = cbrt_coeffs(n, m)
+    return (0 if exact else 1), _darr(p), len(p) - 1, _darr(q or [1.0]), ((len(q) - 1) if q is not None else -1)
+
+
+def lab_linear(x, exact=False, n=4, m=4, rgbdef=None):
+    """CIELAB of LINEAR RGB x, shape (N, 3, ...) -> same shape (FP64)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    nb, hw = x.shape[0], x[0, 0].size
+    out = np.empty_like(x)
+    d = rgbdef or bt709_d65()
+    mode, pa, pn, qa, qm = _lab_args(exact, n, m)
+    lib().orc_lab_linear(ctypes.byref(d), mode, pa, pn, qa, qm, _ptr(x, _D), nb, hw, _ptr(out, _D))
+    return out
+
+
+def lab_loss_grad(x, target, exact=False, n=4, m=4, rgbdef=None, grad=True):
+    """(mean Delta E*ab of lab_linear(x) vs target, analytic dLoss/dx)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    t = np.ascontiguousarray(target, dtype=np.float64)
+    nb, hw = x.shape[0], x[0, 0].size
+    g = np.empty_like(x) if grad else None
+    d = rgbdef or bt709_d65()
+    mode, pa, pn, qa, qm = _lab_args(exact, n, m)
+    loss = lib().orc_lab_loss_grad(ctypes.byref(d), mode, pa, pn, qa, qm, _ptr(x, _D), _ptr(t, _D), nb, hw,
+                                   _ptr(g, _D) if grad else None)
+    return loss, g

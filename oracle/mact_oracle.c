@@ -555,3 +555,99 @@ ORC_API void orc_cube_eps_lut(const orc_rgbdef *d, int method, const float *lut,
     out[0] = sum / 16777216.0;
     out[1] = mx;
 }
+
+/* ------------------------------------------- differentiable RGB -> CIELAB */
+/* Input is LINEAR RGB (the output of Eq. equ_rgb_lin), planar (N, 3, HW).
+ * Lab follows Eq. equ_rgb_xyz and equ_xyz_lab; the loss is the mean over
+ * pixels of Delta E*ab (Eq. equ_cielab_dist) against a target Lab image
+ * (N, 3, HW).  The gradient is the analytic derivative of that loss:
+ *   dLoss/dLab = (Lab - target) / (npix * Delta E)   (0 where Delta E = 0)
+ *   dLab/df:     L = 116 f_y - 16, a = 500 (f_x - f_y), b = 200 (f_y - f_z)
+ *   df/dt:       exact 1/(3 t^(2/3)); approximant (p'q - p q')/q^2;
+ *                7.787 on the linear segment t <= 0.008856
+ *   dt/dRGB:     rows of the matrix divided by the white point. */
+
+static double orc_dpoly(const double *a, int n, double x)
+{
+    double s = 0.0, xp = 1.0;
+    for (int i = 1; i <= n; ++i) {
+        s += i * a[i] * xp;
+        xp *= x;
+    }
+    return s;
+}
+
+/* f(t) and f'(t); mode 0 exact, 1 approximant p/q (m < 0: polynomial). */
+static void orc_f_and_df(int mode, const double *p, int n, const double *q, int m, double t, double *f, double *df)
+{
+    if (t <= 0.008856) {
+        *f = 7.787 * t + 16.0 / 116.0;
+        *df = 7.787;
+        return;
+    }
+    if (!mode) {
+        *f = cbrt(t);
+        *df = 1.0 / (3.0 * cbrt(t * t));
+        return;
+    }
+    double pv = orc_poly(p, n, t), dp = orc_dpoly(p, n, t);
+    double qv = m >= 0 ? orc_poly(q, m, t) : 1.0, dq = m >= 0 ? orc_dpoly(q, m, t) : 0.0;
+    *f = pv / qv;
+    *df = (dp * qv - pv * dq) / (qv * qv);
+}
+
+/* Lab of linear RGB (N, 3, HW) -> (N, 3, HW). */
+ORC_API void orc_lab_linear(const orc_rgbdef *d, int mode, const double *p, int n, const double *q, int m,
+                            const double *x, int64_t nb, int64_t hw, double *lab)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nb * hw; ++k) {
+        int64_t b = k / hw, i = k % hw;
+        const double *xb = x + b * 3 * hw;
+        double f[3], df;
+        for (int c = 0; c < 3; ++c) {
+            double xyz = d->m[3 * c] * xb[i] + d->m[3 * c + 1] * xb[hw + i] + d->m[3 * c + 2] * xb[2 * hw + i];
+            orc_f_and_df(mode, p, n, q, m, xyz / d->white[c], &f[c], &df);
+        }
+        double lab3[3];
+        orc_lab_from_f(f[0], f[1], f[2], lab3);
+        for (int c = 0; c < 3; ++c) lab[b * 3 * hw + c * hw + i] = lab3[c];
+    }
+}
+
+/* Mean Delta E*ab loss against target Lab and its gradient w.r.t. x. */
+ORC_API double orc_lab_loss_grad(const orc_rgbdef *d, int mode, const double *p, int n, const double *q, int m,
+                                 const double *x, const double *target, int64_t nb, int64_t hw, double *grad)
+{
+    const double npix = (double)(nb * hw);
+    double total = 0.0;
+#pragma omp parallel for reduction(+:total) schedule(static)
+    for (int64_t k = 0; k < nb * hw; ++k) {
+        int64_t b = k / hw, i = k % hw;
+        const double *xb = x + b * 3 * hw;
+        const double *tb = target + b * 3 * hw;
+        double f[3], df[3];
+        for (int c = 0; c < 3; ++c) {
+            double xyz = d->m[3 * c] * xb[i] + d->m[3 * c + 1] * xb[hw + i] + d->m[3 * c + 2] * xb[2 * hw + i];
+            orc_f_and_df(mode, p, n, q, m, xyz / d->white[c], &f[c], &df[c]);
+        }
+        double lab3[3];
+        orc_lab_from_f(f[0], f[1], f[2], lab3);
+        double dl = lab3[0] - tb[i], da = lab3[1] - tb[hw + i], dbb = lab3[2] - tb[2 * hw + i];
+        double de = sqrt(dl * dl + da * da + dbb * dbb);
+        total += de;
+        if (!grad) continue;
+        double gL = 0.0, ga = 0.0, gb = 0.0;
+        if (de > 0.0) {
+            gL = dl / (de * npix);
+            ga = da / (de * npix);
+            gb = dbb / (de * npix);
+        }
+        double gf[3] = {500.0 * ga, 116.0 * gL - 500.0 * ga + 200.0 * gb, -200.0 * gb};
+        double gt[3];
+        for (int c = 0; c < 3; ++c) gt[c] = gf[c] * df[c] / d->white[c];
+        for (int j = 0; j < 3; ++j)
+            grad[b * 3 * hw + j * hw + i] = d->m[j] * gt[0] + d->m[3 + j] * gt[1] + d->m[6 + j] * gt[2];
+    }
+    return total / npix;
+}

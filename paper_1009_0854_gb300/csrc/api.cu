@@ -129,6 +129,10 @@ static mact_status build_coeffs(const mact_config &cfg, Coeffs &co)
             co.lab_d[i] = (float)(p[i] - q[i]);   // f = 1 + (p - q)/q
             co.lab_q[i] = (float)q[i];
         }
+        for (int i = 0; i < 4; ++i) {             // derivatives, for the backward
+            co.lab_dd[i] = (float)((i + 1) * (p[i + 1] - q[i + 1]));
+            co.lab_dq[i] = (float)((i + 1) * q[i + 1]);
+        }
         co.lab_rational = 1;
     }
 
@@ -255,6 +259,7 @@ mact_status mact_create(const mact_config *cfg, mact_handle *out)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_kernel, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_lut, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_grad, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         st = cuda_status(e, "mact_create");
         mact_destroy(h);
@@ -275,6 +280,8 @@ mact_status mact_destroy(mact_handle h)
     if (h->ev_kernel) cudaEventDestroy(h->ev_kernel);
     if (h->d_lut4) cudaFree(h->d_lut4);
     if (h->ev_lut) cudaEventDestroy(h->ev_lut);
+    if (h->d_partial) cudaFree(h->d_partial);
+    if (h->ev_grad) cudaEventDestroy(h->ev_grad);
     delete h;
     return MACT_OK;
 }
@@ -382,6 +389,58 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
     if (e == cudaSuccess) e = launch_lut_interp(*h, method, d_lut, n, d_rgb, npix, d_out, d_sel, h->d_lut4, s);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_lut, s);
     return cuda_status(e, "mact_lut_interp launch");
+}
+
+// ---- differentiable RGB -> CIELAB ------------------------------------------
+
+static mact_status check_grad(mact_handle h, int64_t nbatch, int64_t hw, const char *who)
+{
+    if (!h) return inval(who);
+    if (h->cfg.exact == 0 && h->co.lab_rational == 0) {
+        set_error("gradients are provided for the rational cube-root approximants and the exact form");
+        return MACT_E_UNSUPPORTED;
+    }
+    if (nbatch < 0 || hw < 0) return inval("negative size");
+    if (nbatch * hw >= (int64_t(1) << 32)) return inval("more than 2^32 - 1 pixels");
+    return MACT_OK;
+}
+
+mact_status mact_lab_forward(mact_handle h, const float *d_x, int64_t nbatch, int64_t hw, float *d_lab,
+                             mact_stream stream)
+{
+    mact_status st = check_grad(h, nbatch, hw, "mact_lab_forward: NULL handle");
+    if (st != MACT_OK) return st;
+    if (nbatch * hw == 0) return MACT_OK;
+    if (!d_x || !d_lab) return inval("NULL pointer");
+    return cuda_status(launch_lab_forward(*h, d_x, nbatch, hw, d_lab, (cudaStream_t)stream), "mact_lab_forward");
+}
+
+mact_status mact_lab_backward(mact_handle h, const float *d_x, const float *d_grad_lab, int64_t nbatch, int64_t hw,
+                              float *d_grad_x, mact_stream stream)
+{
+    mact_status st = check_grad(h, nbatch, hw, "mact_lab_backward: NULL handle");
+    if (st != MACT_OK) return st;
+    if (nbatch * hw == 0) return MACT_OK;
+    if (!d_x || !d_grad_lab || !d_grad_x) return inval("NULL pointer");
+    return cuda_status(launch_lab_backward(*h, d_x, d_grad_lab, nbatch, hw, d_grad_x, (cudaStream_t)stream),
+                       "mact_lab_backward");
+}
+
+mact_status mact_lab_delta_e_loss(mact_handle h, const float *d_x, const float *d_target_lab, int64_t nbatch,
+                                  int64_t hw, float *d_loss, float *d_grad_x, mact_stream stream)
+{
+    mact_status st = check_grad(h, nbatch, hw, "mact_lab_delta_e_loss: NULL handle");
+    if (st != MACT_OK) return st;
+    if (nbatch * hw == 0) return inval("empty input: the mean is undefined");
+    if (!d_x || !d_target_lab || !d_loss) return inval("NULL pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(h->grad_mu);
+    cudaError_t e = cudaSuccess;
+    if (!h->d_partial) e = cudaMalloc(&h->d_partial, (size_t)h->num_sms * 8 * sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_grad, 0);   // previous reader of the partials
+    if (e == cudaSuccess) e = launch_lab_delta_e(*h, d_x, d_target_lab, nbatch, hw, d_loss, d_grad_x, h->d_partial, s);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_grad, s);
+    return cuda_status(e, "mact_lab_delta_e_loss");
 }
 
 const char *mact_strerror(mact_status st)

@@ -26,6 +26,8 @@ struct Coeffs {
     float m[9];          // rgb_to_xyz row c divided by white[c]
     float lab_d[6];      // rational: p - q (degree 4); polynomial: p (degree 5)
     float lab_q[5];      // rational: q (degree 4)
+    float lab_dd[4];     // rational: d' = (p - q)' (degree 3)
+    float lab_dq[4];     // rational: q' (degree 3)
     int32_t lab_rational;
     float hsi[6];        // arctan(sqrt(3) x) on |x| <= 1, degree 5
     float sct_p[6];      // 2 arcsin(y/sqrt 2), y = sqrt(1 - B/L), degree 5

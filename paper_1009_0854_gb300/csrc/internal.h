@@ -30,6 +30,11 @@ struct mact_ctx {
     float4 *d_lut4 = nullptr;
     int64_t lut4_cap = 0;                // nodes
     cudaEvent_t ev_lut = nullptr;        // last interpolation kernel that read d_lut4
+
+    // differentiable CIELAB: per-CTA partial sums of the loss (SMs x 8 doubles)
+    std::mutex grad_mu;
+    double *d_partial = nullptr;
+    cudaEvent_t ev_grad = nullptr;       // last loss reduction that read d_partial
 };
 
 namespace mact {
@@ -51,6 +56,14 @@ cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut,
                               int32_t *d_sel, const float4 *d_lut4, cudaStream_t s);
 cudaError_t launch_lut_pack4(const float *d_lut, int n, float4 *d_lut4, cudaStream_t s);
 bool lut_needs_pack(int n);
+
+// k_grad.cu
+cudaError_t launch_lab_forward(const mact_ctx &h, const float *x, int64_t nb, int64_t hw, float *lab,
+                               cudaStream_t s);
+cudaError_t launch_lab_backward(const mact_ctx &h, const float *x, const float *glab, int64_t nb, int64_t hw,
+                                float *gx, cudaStream_t s);
+cudaError_t launch_lab_delta_e(const mact_ctx &h, const float *x, const float *tgt, int64_t nb, int64_t hw,
+                               float *loss, float *gx, double *partial, cudaStream_t s);
 
 // tile count of an image in the streaming engine
 int64_t tiles_of(const ImageDesc &im);

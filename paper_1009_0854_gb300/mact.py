@@ -95,6 +95,11 @@ def lib():
         for name in ("mact_serve_create", "mact_serve_submit", "mact_serve_poll", "mact_serve_wait",
                      "mact_serve_cancel", "mact_serve_release", "mact_serve_stats", "mact_serve_destroy"):
             getattr(L, name).restype = ctypes.c_int
+        L.mact_lab_forward.argtypes = [_VP, _VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP]
+        L.mact_lab_backward.argtypes = [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP]
+        L.mact_lab_delta_e_loss.argtypes = [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP]
+        for name in ("mact_lab_forward", "mact_lab_backward", "mact_lab_delta_e_loss"):
+            getattr(L, name).restype = ctypes.c_int
         L.mact_strerror.argtypes = [ctypes.c_int]
         L.mact_strerror.restype = ctypes.c_char_p
         L.mact_last_error.argtypes = []
@@ -256,6 +261,47 @@ def mact_lut_interp(h, method, lut, rgb, out=None, sel=False, stream=None):
                                  ctypes.byref(ptrs), _VP(s.data_ptr() if s is not None else 0),
                                  _stream(stream)), "mact_lut_interp")
     return (out, s) if sel else out
+
+
+# ------------------------------------------------ differentiable CIELAB
+
+def _planar(x):
+    if x.dtype != torch.float32 or not x.is_contiguous() or x.dim() < 2 or x.shape[1] != 3:
+        raise ValueError("expected a contiguous float32 tensor of shape (N, 3, ...)")
+    nb = x.shape[0]
+    return nb, (x.numel() // (3 * nb)) if nb else 0
+
+
+def mact_lab_forward(h, x, out=None, stream=None):
+    """CIELAB of linear RGB x (N, 3, ...) -> same shape."""
+    nb, hw = _planar(x)
+    out = torch.empty_like(x) if out is None else out
+    _check(lib().mact_lab_forward(h.ptr, _VP(x.data_ptr()), nb, hw, _VP(out.data_ptr()), _stream(stream)),
+           "mact_lab_forward")
+    return out
+
+
+def mact_lab_backward(h, x, grad_lab, out=None, stream=None):
+    """Vector-Jacobian product J(x)^T grad_lab."""
+    nb, hw = _planar(x)
+    grad_lab = grad_lab.contiguous()
+    out = torch.empty_like(x) if out is None else out
+    _check(lib().mact_lab_backward(h.ptr, _VP(x.data_ptr()), _VP(grad_lab.data_ptr()), nb, hw,
+                                   _VP(out.data_ptr()), _stream(stream)), "mact_lab_backward")
+    return out
+
+
+def mact_lab_delta_e_loss(h, x, target_lab, grad=True, loss=None, grad_out=None, stream=None):
+    """(mean Delta E*ab of Lab(x) vs target_lab as a 0-d tensor, dLoss/dx or None)."""
+    nb, hw = _planar(x)
+    if target_lab.shape != x.shape or not target_lab.is_contiguous():
+        raise ValueError("target_lab must be contiguous with the shape of x")
+    loss = torch.empty((), dtype=torch.float32, device=x.device) if loss is None else loss
+    g = (torch.empty_like(x) if grad_out is None else grad_out) if grad else None
+    _check(lib().mact_lab_delta_e_loss(h.ptr, _VP(x.data_ptr()), _VP(target_lab.data_ptr()), nb, hw,
+                                       _VP(loss.data_ptr()), _VP(g.data_ptr() if g is not None else 0),
+                                       _stream(stream)), "mact_lab_delta_e_loss")
+    return loss, g
 
 
 # ------------------------------------------------------------- served form

@@ -1,0 +1,134 @@
+"""GPU parity of the differentiable RGB -> CIELAB: forward, vector-Jacobian
+product and the fused mean Delta E*ab loss + gradient against the FP64
+oracle, plus torch.autograd.gradcheck of the autograd wrapper."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import tables
+from paper_1009_0854_gb300 import autograd, mact, synth
+from parity import LAB_TOL
+
+pytestmark = pytest.mark.gpu
+
+KNEE = 0.008856
+
+
+@pytest.fixture(scope="module", params=[0, 1], ids=["mact", "exact"])
+def hx(request):
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return mact.mact_create(exact=request.param), bool(request.param)
+
+
+def _inputs(n=3, h=40, w=52, seed=0):
+    x, tgt_rgb = synth.linear_rgb_batch(n=n, h=h, w=w, seed=seed)
+    return x, O.lab_linear(tgt_rgb).astype(np.float32)
+
+
+def _near_knee(x):
+    """Pixels whose FP64 t lies within 1e-7 of the knee on some channel: FP32
+    and FP64 may pick different branches there."""
+    M = np.array(tables.BT709_MATRIX).reshape(3, 3) / np.array(tables.D65_WHITE)[:, None]
+    t = np.einsum("cj,njp->ncp", M, x.reshape(x.shape[0], 3, -1).astype(np.float64))
+    return (np.abs(t - KNEE) < 1e-7).any(axis=1).reshape(x.shape[0], *x.shape[2:])
+
+
+def test_forward_matches_oracle(hx):
+    h, exact = hx
+    x, _ = _inputs()
+    lab = mact.mact_lab_forward(h, torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = O.lab_linear(x, exact=exact)
+    ok = ~_near_knee(x)[:, None]
+    assert np.abs(np.where(ok, lab - ref, 0.0)).max() <= LAB_TOL
+
+
+def test_fused_loss_and_gradient_match_oracle(hx):
+    h, exact = hx
+    x, tgt = _inputs(seed=1)
+    loss, g = mact.mact_lab_delta_e_loss(h, torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda())
+    torch.cuda.synchronize()
+    rl, rg = O.lab_loss_grad(x, tgt, exact=exact)
+    assert float(loss) == pytest.approx(rl, rel=2e-6)
+    g = g.cpu().numpy()
+    ok = ~_near_knee(x)[:, None]
+    scale = np.abs(rg).max()
+    err = np.abs(np.where(ok, g - rg, 0.0))
+    assert err.max() <= 1e-4 * scale
+    # relative agreement elementwise where the gradient is not tiny
+    big = ok & (np.abs(rg) > 1e-3 * scale)
+    assert (np.abs(g - rg)[big] / np.abs(rg)[big]).max() <= 2e-3
+
+
+def test_vjp_matches_oracle_and_fused(hx):
+    """backward(x, dLoss/dLab) equals the fused gradient when dLoss/dLab is
+    the Delta E direction divided by the pixel count."""
+    h, exact = hx
+    x, tgt = _inputs(seed=2)
+    xt = torch.from_numpy(x).cuda()
+    lab = mact.mact_lab_forward(h, xt)
+    d = lab - torch.from_numpy(tgt).cuda()
+    de = d.norm(dim=1, keepdim=True)
+    glab = torch.where(de > 0, d / de, torch.zeros_like(d)) / (x.shape[0] * x[0, 0].size)
+    g1 = mact.mact_lab_backward(h, xt, glab)
+    _, g2 = mact.mact_lab_delta_e_loss(h, xt, torch.from_numpy(tgt).cuda())
+    torch.cuda.synchronize()
+    scale = g2.abs().max().item()
+    assert (g1 - g2).abs().max().item() <= 1e-4 * scale
+
+
+def test_autograd_gradcheck(hx):
+    """torch.autograd.gradcheck of the Lab wrapper (FP32, central differences
+    with eps = 1e-3) on inputs away from the knee."""
+    h, _ = hx
+    rng = np.random.default_rng(3)
+    x = torch.from_numpy(rng.uniform(0.2, 0.9, size=(1, 3, 4)).astype(np.float32)).cuda().requires_grad_()
+    fn = lambda v: autograd.lab(v, h)
+    assert torch.autograd.gradcheck(fn, (x,), eps=1e-3, atol=5e-2, rtol=2e-2, nondet_tol=0.0)
+
+
+def test_loss_autograd_and_knee_sides(hx):
+    """The fused loss through autograd; gray pixels on either side of the knee
+    get the one-sided derivative of their own branch (oracle)."""
+    h, exact = hx
+    eps = 3e-5
+    x = np.empty((1, 3, 4), dtype=np.float32)
+    x[0, :, 0] = KNEE + eps
+    x[0, :, 1] = KNEE - eps
+    x[0, :, 2] = 0.0
+    x[0, :, 3] = 0.6
+    tgt = np.array([[[10, 20, 0, 50], [5, -5, 1, 3], [-3, 4, 0, -2]]], dtype=np.float32)
+    xt = torch.from_numpy(x).cuda().requires_grad_()
+    loss = autograd.delta_e_loss(xt, torch.from_numpy(tgt).cuda(), h)
+    loss.backward()
+    rl, rg = O.lab_loss_grad(x, tgt, exact=exact)
+    assert loss.item() == pytest.approx(rl, rel=1e-5)
+    assert np.abs(xt.grad.cpu().numpy() - rg).max() <= 1e-3 * np.abs(rg).max()
+
+
+def test_unaligned_and_odd_sizes(hx):
+    """hw not a multiple of 4 and an offset view take the scalar path."""
+    h, exact = hx
+    x, tgt = _inputs(n=2, h=7, w=9, seed=4)
+    big = torch.zeros(x.size + 1, device="cuda")
+    xt = big[1:].view(x.shape)
+    xt.copy_(torch.from_numpy(x))
+    loss, g = mact.mact_lab_delta_e_loss(h, xt, torch.from_numpy(tgt).cuda())
+    rl, rg = O.lab_loss_grad(x, tgt, exact=exact)
+    assert float(loss) == pytest.approx(rl, rel=2e-6)
+    assert np.abs(g.cpu().numpy() - rg).max() <= 1e-3 * np.abs(rg).max()
+
+
+def test_full_size_workload_properties(hx):
+    """The 64 x 3 x 512 x 512 workload: the loss matches the oracle on the
+    whole tensor; gradients match on a sample of images."""
+    h, exact = hx
+    x, tgt_rgb = synth.linear_rgb_batch(n=64, h=512, w=512, seed=0)
+    tgt = O.lab_linear(tgt_rgb).astype(np.float32)
+    loss, g = mact.mact_lab_delta_e_loss(h, torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda())
+    torch.cuda.synchronize()
+    rl, rg = O.lab_loss_grad(x, tgt, exact=exact)
+    assert float(loss) == pytest.approx(rl, rel=1e-5)
+    g = g.cpu().numpy()
+    ok = ~_near_knee(x)[:, None]
+    assert np.abs(np.where(ok, g - rg, 0.0)).max() <= 2e-4 * np.abs(rg).max()
