@@ -362,6 +362,174 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------ other workloads (reported in the design doc)
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_batch_workload(args):
+    """256 uneven images (log-uniform sides in [64, 4096], mixed content and
+    spaces): one batched launch vs per-image launches (MACT) vs per-image exact
+    launches (plain), FP32 and FP16 outputs."""
+    import torch
+    from paper_1009_0854_gb300 import mact, synth
+    dev = torch.device("cuda", 0)
+    specs = synth.batch_images(count=256, seed=0)
+    imgs = [(torch.from_numpy(im).to(dev), space) for im, space in specs]
+    npx = sum(r.shape[0] * r.shape[1] for r, _ in imgs)
+    h = mact.mact_create()
+    he = mact.mact_create(exact=1)
+    out = {}
+    for dt, name in ((torch.float32, "f32"), (torch.float16, "f16")):
+        outs = [torch.empty((3,) + tuple(r.shape[:2]), dtype=dt, device=dev) for r, _ in imgs]
+        table, shape = mact.mact_autotune_batch(h, imgs, outs=outs, reps=3)
+        plan, _ = mact.mact_batch_plan_create(h, imgs, outs=outs)
+
+        def t(fn, k=args.steps):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            a, b = _events(torch)
+            a.record()
+            for _ in range(k):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / k
+
+        ms_graph = t(plan.graph_launch)
+        ms_batch = t(lambda: mact.mact_convert_batch(h, imgs, outs=outs))
+        ms_single = t(lambda: [mact.mact_convert(h, r, s, out=o) for (r, s), o in zip(imgs, outs)])
+        ms_plain = t(lambda: [mact.mact_convert(he, r, s, out=o) for (r, s), o in zip(imgs, outs)])
+        bpp = 3 + 3 * (4 if dt == torch.float32 else 2)
+        hbm, _ = peaks()
+        out[name] = {"graph_gpix_s": round(npx / ms_graph / 1e6, 2), "batch_gpix_s": round(npx / ms_batch / 1e6, 2),
+                     "per_image_mact_gpix_s": round(npx / ms_single / 1e6, 2),
+                     "per_image_exact_gpix_s": round(npx / ms_plain / 1e6, 2),
+                     "graph_hbm_frac": round(npx * bpp / (ms_graph * 1e-3) / 1e9 / hbm, 4),
+                     "autotuned_shape": {"threads": shape[0], "px_per_thread": shape[1], "ctas_per_sm": shape[2]},
+                     "tune_table_ms": {"%dx%d/%d" % (r["threads"], r["px_per_thread"], r["ctas_per_sm"]):
+                                       round(r["ms"], 4) for r in table}}
+        plan.close()
+    print(json.dumps({"workload": "batch: 256 uneven images, %d px" % npx, "rows": out}))
+
+
+def run_grad_workload(args):
+    """Fused forward + mean Delta E*ab + backward on 64 x 3 x 512 x 512."""
+    import torch
+    from paper_1009_0854_gb300 import mact, synth
+    dev = torch.device("cuda", 0)
+    x, tgt_rgb = synth.linear_rgb_batch(n=64, h=512, w=512, seed=0)
+    xt = torch.from_numpy(x).to(dev)
+    rows = {}
+    for exact in (0, 1):
+        h = mact.mact_create(exact=exact)
+        tgt = mact.mact_lab_forward(h, torch.from_numpy(tgt_rgb).to(dev))
+        loss = torch.empty((), device=dev)
+        g = torch.empty_like(xt)
+        for _ in range(3):
+            mact.mact_lab_delta_e_loss(h, xt, tgt, loss=loss, grad_out=g)
+        torch.cuda.synchronize()
+        a, b = _events(torch)
+        a.record()
+        for _ in range(args.steps):
+            mact.mact_lab_delta_e_loss(h, xt, tgt, loss=loss, grad_out=g)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        npx = x.shape[0] * x.shape[2] * x.shape[3]
+        hbm, _ = peaks()
+        rows["exact" if exact else "mact"] = {"ms": round(ms, 4), "gpix_s": round(npx / ms / 1e6, 2),
+                                              "hbm_frac": round(npx * 36 / (ms * 1e-3) / 1e9 / hbm, 4),
+                                              "loss": float(loss)}
+    print(json.dumps({"workload": "grad: fused mean-DeltaE loss + backward, 64x3x512x512 FP32", "rows": rows}))
+
+
+def run_serve_workload(args):
+    """Poisson arrivals (2000/s) of 0.1-24 Mpx images, 50/25/25% CIELAB/HSI/SCT,
+    pinned host input and output, through the continuous-batching server
+    (MACT, 16 GB staging budget) and through the plain path (one request at a
+    time: H2D, exact-libm kernel, D2H)."""
+    import torch
+    from paper_1009_0854_gb300 import mact, synth
+    dev = torch.device("cuda", 0)
+    trace = synth.serve_trace(rate=2000.0, duration=args.serve_seconds, seed=0)
+    maxpx = max(h * w for _, h, w, _, _ in trace)
+    pool = torch.from_numpy(synth.request_image(4096, 6144, 2, 7).reshape(-1)).pin_memory()  # 75 MB of content
+    nbuf = 24
+    outs = [torch.empty(3 * maxpx, dtype=torch.float32).pin_memory() for _ in range(nbuf)]
+
+    def req_views(i, hgt, wid):
+        inp = pool[: hgt * wid * 3].view(hgt, wid, 3)
+        out = outs[i % nbuf][: 3 * hgt * wid].view(3, hgt, wid)
+        return inp, out
+
+    results = {}
+    # served
+    h = mact.mact_create()
+    srv = mact.mact_serve_create(h, 16 << 30, max_slots=nbuf)
+    pending = {}
+    lat = []
+    npx = 0
+
+    def retire(tk, ta, t_sub):
+        mact.mact_serve_wait(srv, tk, 600000)
+        _, server_ms = mact.mact_serve_poll(srv, tk)
+        mact.mact_serve_release(srv, tk)
+        lat.append((t_sub - ta) * 1e3 + server_ms)     # from arrival: queueing in the driver counts
+
+    t0 = time.perf_counter()
+    for i, (ta, hgt, wid, _, space) in enumerate(trace):
+        while time.perf_counter() - t0 < ta:
+            pass
+        slot = i % nbuf
+        if slot in pending:                       # output buffer reuse: wait for its last user
+            retire(*pending.pop(slot))
+        inp, out = req_views(i, hgt, wid)
+        t_sub = time.perf_counter() - t0
+        tk, _ = mact.mact_serve_submit(srv, inp, space, out=out)
+        pending[slot] = (tk, ta, t_sub)
+        npx += hgt * wid
+    for slot in list(pending):
+        retire(*pending.pop(slot))
+    wall = time.perf_counter() - t0
+    st = mact.mact_serve_stats(srv)
+    srv.close()
+    lat.sort()
+    results["served"] = {"requests": len(trace), "p50_ms": round(lat[len(lat) // 2], 3),
+                         "p99_ms": round(lat[int(0.99 * (len(lat) - 1))], 3), "max_ms": round(lat[-1], 3),
+                         "gpix_s": round(npx / wall / 1e9, 3), "batches": st["batches"],
+                         "server_p50_ms": round(st["p50_ms"], 3), "server_p99_ms": round(st["p99_ms"], 3)}
+    # plain: one request at a time, exact libm kernels
+    he = mact.mact_create(exact=1)
+    dbuf_in = torch.empty(3 * maxpx, dtype=torch.uint8, device=dev)
+    dbuf_out = torch.empty(3 * maxpx, dtype=torch.float32, device=dev)
+    s = torch.cuda.current_stream()
+    lat = []
+    t0 = time.perf_counter()
+    npx = 0
+    for i, (ta, hgt, wid, _, space) in enumerate(trace):
+        while time.perf_counter() - t0 < ta:
+            pass
+        inp, out = req_views(i, hgt, wid)
+        din = dbuf_in[: hgt * wid * 3].view(hgt, wid, 3)
+        dout = dbuf_out[: 3 * hgt * wid].view(3, hgt, wid)
+        din.copy_(inp, non_blocking=True)
+        mact.mact_convert(he, din, space, out=dout, stream=s)
+        out.copy_(dout, non_blocking=True)
+        s.synchronize()
+        lat.append((time.perf_counter() - t0 - ta) * 1e3)
+        npx += hgt * wid
+    wall = time.perf_counter() - t0
+    lat.sort()
+    results["plain_exact_per_image"] = {"requests": len(trace), "p50_ms": round(lat[len(lat) // 2], 3),
+                                        "p99_ms": round(lat[int(0.99 * (len(lat) - 1))], 3),
+                                        "max_ms": round(lat[-1], 3), "gpix_s": round(npx / wall / 1e9, 3)}
+    print(json.dumps({"workload": "serve: Poisson 2000 req/s for %g s, 0.1-24 Mpx, pinned host buffers"
+                      % args.serve_seconds, "rows": results}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,10 +540,20 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=1 << 22)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cube", choices=["cube", "batch", "serve", "grad"],
+                    help="cube: the default step; the others measure the batched, served and "
+                         "differentiable forms on their own workloads")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch_workload(args)
+    elif args.workload == "serve":
+        run_serve_workload(args)
+    elif args.workload == "grad":
+        run_grad_workload(args)
     else:
         run_gpu(args)
 

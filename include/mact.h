@@ -48,6 +48,7 @@ extern "C" {
 
 typedef struct mact_ctx *mact_handle;
 typedef struct mact_server *mact_server_t;
+typedef struct mact_batch_plan *mact_batch_plan_t;
 typedef void *mact_stream; /* cudaStream_t */
 
 typedef enum {
@@ -144,6 +145,50 @@ mact_status mact_convert(mact_handle h, const mact_image *img, mact_stream strea
  * Result of each image equals mact_convert of that image. */
 mact_status mact_convert_batch(mact_handle h, const mact_image *imgs, int32_t count,
                                mact_stream stream);
+
+/* ---- batched form for a repeated image list ------------------------------
+ * A plan fixes one list of images (the pointers, sizes, spaces and dtypes of
+ * imgs at creation) and the handle's current batch launch shape.  Creation
+ * validates the list and uploads its device work list once (synchronously);
+ * each launch is then one kernel with no host work, no copy and no
+ * allocation, so it may be captured into a CUDA graph.  The images' contents
+ * may change between launches; their addresses and shapes may not.  Launches
+ * of one plan must not overlap on the GPU (they share the plan's counters). */
+mact_status mact_batch_plan_create(mact_handle h, const mact_image *imgs, int32_t count, mact_batch_plan_t *out);
+
+/* Launch the plan on stream (the same kernel as mact_convert_batch). */
+mact_status mact_batch_plan_launch(mact_batch_plan_t plan, mact_stream stream);
+
+/* Launch the plan through a CUDA graph: the first call captures one launch
+ * on a private stream and instantiates the graph; every call replays it on
+ * stream. */
+mact_status mact_batch_plan_graph_launch(mact_batch_plan_t plan, mact_stream stream);
+
+/* Free the plan (synchronises the device first). */
+mact_status mact_batch_plan_destroy(mact_batch_plan_t plan);
+
+/* One timed launch shape of the batched kernel. */
+typedef struct {
+    int32_t threads;        /* threads per CTA */
+    int32_t px_per_thread;  /* pixels per thread per tile (tile = threads * px_per_thread) */
+    int32_t ctas_per_sm;    /* resident CTAs per SM of the persistent grid */
+    float ms;               /* mean time of one launch over imgs */
+} mact_tune_entry;
+
+/* Autotuner: time every supported launch shape of the batched kernel
+ * (threads per CTA 128/256/512, 16 or 32 pixels per thread, full or half
+ * residency) on the caller's images (reps launches each, after 2 warm-ups,
+ * on a private stream; the images are converted repeatedly), keep the fastest
+ * as the handle's batch shape (used by mact_convert_batch and later plans),
+ * and report up to table_cap timings in table. */
+mact_status mact_autotune_batch(mact_handle h, const mact_image *imgs, int32_t count, int32_t reps,
+                                mact_tune_entry *table, int32_t table_cap, int32_t *n_entries);
+
+/* Set / read the handle's batch launch shape directly (for example from a
+ * cached autotuning result).  Unsupported shapes give MACT_E_UNSUPPORTED;
+ * ctas_per_sm 0 means as many as fit. */
+mact_status mact_set_batch_shape(mact_handle h, int32_t threads, int32_t px_per_thread, int32_t ctas_per_sm);
+mact_status mact_get_batch_shape(mact_handle h, int32_t *threads, int32_t *px_per_thread, int32_t *ctas_per_sm);
 
 /* Same result as mact_convert_batch, without any memory allocation.  The
  * paper has no counterpart: this exists for callers that cannot allocate

@@ -189,7 +189,7 @@ mact_status check_image(const mact_image *img)
     return MACT_OK;
 }
 
-ImageDesc make_desc(const mact_image &img)
+ImageDesc make_desc(const mact_image &img, int64_t tile_px)
 {
     ImageDesc d{};
     d.rgb = img.rgb;
@@ -208,7 +208,7 @@ ImageDesc make_desc(const mact_image &img)
         d.pitch = img.pitch_bytes;
         d.opitch = img.out_pitch_elems;
     }
-    d.tiles_per_row = (d.width + kTile - 1) / kTile;
+    d.tiles_per_row = (d.width + tile_px - 1) / tile_px;
     return d;
 }
 
@@ -326,11 +326,12 @@ mact_status mact_convert_batch(mact_handle h, const mact_image *imgs, int32_t co
         if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch: work list allocation");
         h->work_cap = cap;
     }
+    const BatchCfg cfg = h->batch_cfg;
     int64_t total = 0;
     int32_t n = 0;
     for (int32_t i = 0; i < count; ++i) {
         if (imgs[i].width == 0 || imgs[i].height == 0) continue;
-        ImageDesc d = make_desc(imgs[i]);
+        ImageDesc d = make_desc(imgs[i], cfg.tile_px());
         d.tile_begin = total;
         total += tiles_of(d);
         h->h_work[n++] = d;
@@ -342,10 +343,11 @@ mact_status mact_convert_batch(mact_handle h, const mact_image *imgs, int32_t co
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_imgs, h->h_work, n * sizeof(ImageDesc), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_copy, s);
     if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch: work list copy");
-    if (h->batch_blocks_per_sm == 0) h->batch_blocks_per_sm = batch_blocks_per_sm(*h);
-    int64_t grid = (int64_t)h->num_sms * h->batch_blocks_per_sm;
+    int per_sm = batch_blocks_per_sm(*h, cfg);
+    if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
+    int64_t grid = (int64_t)h->num_sms * per_sm;
     if (grid > total) grid = total;
-    e = launch_batch(*h, d_imgs, n, total, d_ctr, (int)grid, s);
+    e = launch_batch(*h, d_imgs, n, total, d_ctr, (int)grid, s, cfg);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_kernel, s);
     return cuda_status(e, "mact_convert_batch launch");
 }

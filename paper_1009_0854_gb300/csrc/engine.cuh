@@ -5,12 +5,13 @@
 // The work is HBM-bound by design (3 bytes read, 12 (FP32) or 6 (FP16) bytes
 // written per pixel, nothing reused), so the engine's job is to keep the
 // per-pixel instruction count low and the memory system busy:
-//   * a tile is THREADS x 16 pixels (12*THREADS input bytes); every thread
-//     loads exactly three 16-byte vectors of it (coalesced, streaming hint)
-//     and stages them in shared memory;
+//   * a tile is THREADS x 4*SUBS pixels (SUBS = 4 or 8 sub-blocks; 12 or 24
+//     bytes of input per thread); every thread loads exactly 3*SUBS/4 16-byte
+//     vectors of it (coalesced, streaming hint) and stages them in shared
+//     memory;
 //   * each thread then de-interleaves 4 consecutive pixels at a time from
 //     three 32-bit shared-memory words (stride 3 words across a warp: no bank
-//     conflicts), four times per tile, and writes each plane's 4 results as
+//     conflicts), SUBS times per tile, and writes each plane's 4 results as
 //     one 16-byte (FP32) or 8-byte (FP16) streaming store -- a warp writes
 //     512 contiguous bytes per store instruction;
 //   * for contiguous, aligned images the persistent loop prefetches the next
@@ -24,20 +25,21 @@
 
 namespace mact {
 
-constexpr int kSubBlocks = 4;                        // 4 pixels per thread per sub-block
+constexpr int kSubBlocks = 4;                        // default sub-blocks per tile
 
-template <int THREADS>
+template <int THREADS, int SUBS = kSubBlocks>
 struct TileShape {
+    static_assert(SUBS % 4 == 0, "whole 16-byte vectors per thread");
     static constexpr int sub = THREADS * kPxPerThread;   // pixels per sub-block
-    static constexpr int px = sub * kSubBlocks;          // pixels per tile
-    static constexpr int vecs = px * 3 / 16;             // 16-byte input vectors per tile
-    static_assert(vecs == 3 * THREADS, "three input vectors per thread");
+    static constexpr int px = sub * SUBS;                // pixels per tile
+    static constexpr int vpt = 3 * SUBS / 4;             // 16-byte input vectors per thread
+    static constexpr int vecs = vpt * THREADS;           // 16-byte input vectors per tile
 };
 
-template <int THREADS>
+template <int THREADS, int SUBS = kSubBlocks>
 __host__ __device__ inline int64_t tiles_of_t(const ImageDesc &im)
 {
-    constexpr int P = TileShape<THREADS>::px;
+    constexpr int P = TileShape<THREADS, SUBS>::px;
     if (im.width <= 0 || im.height <= 0) return 0;
     return im.height * ((im.width + P - 1) / P);
 }
@@ -55,19 +57,19 @@ __device__ __forceinline__ bool streamable(const ImageDesc &im, const int32_t *s
     return ok;
 }
 
-template <int THREADS>
-__device__ __forceinline__ void load_tile(uint4 (&v)[3], const uint8_t *in)
+template <int THREADS, int SUBS>
+__device__ __forceinline__ void load_tile(uint4 (&v)[TileShape<THREADS, SUBS>::vpt], const uint8_t *in)
 {
     const uint4 *p = reinterpret_cast<const uint4 *>(in) + threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v[k] = __ldcs(p + k * THREADS);
+    for (int k = 0; k < TileShape<THREADS, SUBS>::vpt; ++k) v[k] = __ldcs(p + k * THREADS);
 }
 
-template <int THREADS>
-__device__ __forceinline__ void stage_tile(uint4 *sbuf, const uint4 (&v)[3])
+template <int THREADS, int SUBS>
+__device__ __forceinline__ void stage_tile(uint4 *sbuf, const uint4 (&v)[TileShape<THREADS, SUBS>::vpt])
 {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) sbuf[threadIdx.x + k * THREADS] = v[k];
+    for (int k = 0; k < TileShape<THREADS, SUBS>::vpt; ++k) sbuf[threadIdx.x + k * THREADS] = v[k];
 }
 
 // Apply op to the 4 pixels of sub-block s owned by this thread.
@@ -84,12 +86,12 @@ __device__ __forceinline__ void apply4(const uint4 *sbuf, int s, const Op &op, f
 }
 
 // Full, aligned tile: sbuf holds its input; outputs start at o* (+ sel).
-template <int THREADS, typename OutT, bool SEL, class Op>
+template <int THREADS, int SUBS, typename OutT, bool SEL, class Op>
 __device__ __forceinline__ void compute_full(const uint4 *sbuf, const Op &op, OutT *o0, OutT *o1, OutT *o2,
                                              int32_t *sel)
 {
 #pragma unroll
-    for (int s = 0; s < kSubBlocks; ++s) {
+    for (int s = 0; s < SUBS; ++s) {
         float v[3][4];
         int sl[4];
         apply4<THREADS>(sbuf, s, op, v, sl);
@@ -104,14 +106,14 @@ __device__ __forceinline__ void compute_full(const uint4 *sbuf, const Op &op, Ou
 // Guarded tile of cnt <= px pixels at any alignment.  Ends with a barrier
 // already passed after the staging; the caller synchronises before reusing
 // sbuf.
-template <int THREADS, typename OutT, bool SEL, class Op>
+template <int THREADS, int SUBS, typename OutT, bool SEL, class Op>
 __device__ __forceinline__ void compute_guarded(uint4 *sbuf, const uint8_t *in, int cnt, const Op &op, OutT *o0,
                                                 OutT *o1, OutT *o2, int32_t *sel)
 {
     uint8_t *sb = reinterpret_cast<uint8_t *>(sbuf);
     for (int i = threadIdx.x; i < 3 * cnt; i += THREADS) sb[i] = in[i];
     __syncthreads();
-    for (int s = 0; s < kSubBlocks; ++s) {
+    for (int s = 0; s < SUBS; ++s) {
         const int p = s * TileShape<THREADS>::sub + kPxPerThread * threadIdx.x;
         if (p >= cnt) break;
         float v[3][4];
@@ -131,11 +133,11 @@ __device__ __forceinline__ void compute_guarded(uint4 *sbuf, const uint8_t *in, 
 
 // Tile t of image im (any geometry): the guarded or, when full and aligned,
 // the vector path.  The caller synchronises before reusing sbuf.
-template <int THREADS, typename OutT, bool SEL, class Op>
+template <int THREADS, typename OutT, bool SEL, class Op, int SUBS = kSubBlocks>
 __device__ __forceinline__ void process_tile(const ImageDesc &im, int64_t t, const Op &op, uint4 *sbuf,
                                              int32_t *sel)
 {
-    constexpr int P = TileShape<THREADS>::px;
+    constexpr int P = TileShape<THREADS, SUBS>::px;
     const uint32_t tpr = (uint32_t)im.tiles_per_row;     // < 2^31 (checked on the host)
     const uint32_t tt = (uint32_t)t;
     const uint32_t row = tt / tpr;
@@ -154,52 +156,52 @@ __device__ __forceinline__ void process_tile(const ImageDesc &im, int64_t t, con
     if (SEL) oa |= reinterpret_cast<uintptr_t>(sl);
     const bool fast = cnt == P && ((reinterpret_cast<uintptr_t>(in) & 15) == 0) && ((oa & omask) == 0);
     if (fast) {
-        uint4 v[3];
-        load_tile<THREADS>(v, in);
-        stage_tile<THREADS>(sbuf, v);
+        uint4 v[TileShape<THREADS, SUBS>::vpt];
+        load_tile<THREADS, SUBS>(v, in);
+        stage_tile<THREADS, SUBS>(sbuf, v);
         __syncthreads();
-        compute_full<THREADS, OutT, SEL>(sbuf, op, o0, o1, o2, sl);
+        compute_full<THREADS, SUBS, OutT, SEL>(sbuf, op, o0, o1, o2, sl);
     } else {
-        compute_guarded<THREADS, OutT, SEL>(sbuf, in, cnt, op, o0, o1, o2, sl);
+        compute_guarded<THREADS, SUBS, OutT, SEL>(sbuf, in, cnt, op, o0, o1, o2, sl);
     }
 }
 
 // Whole image, persistent CTA loop.  Streamable images run the prefetching
 // vector loop over their full tiles and hand the partial last tile to the
 // guarded path; everything else walks tiles through process_tile.
-template <int THREADS, typename OutT, bool SEL, class Op>
+template <int THREADS, typename OutT, bool SEL, class Op, int SUBS = kSubBlocks>
 __device__ __forceinline__ void run_image(const ImageDesc &im, int64_t ntiles, const Op &op, uint4 *sbuf,
                                           int32_t *sel)
 {
-    constexpr int P = TileShape<THREADS>::px;
+    constexpr int P = TileShape<THREADS, SUBS>::px;
     if (streamable<OutT, SEL>(im, sel)) {
         const int64_t nfull = im.width / P;
         OutT *b0 = reinterpret_cast<OutT *>(im.out[0]);
         OutT *b1 = reinterpret_cast<OutT *>(im.out[1]);
         OutT *b2 = reinterpret_cast<OutT *>(im.out[2]);
         int64_t t = blockIdx.x;
-        uint4 v[3];
-        if (t < nfull) load_tile<THREADS>(v, im.rgb + 3 * P * t);
+        uint4 v[TileShape<THREADS, SUBS>::vpt];
+        if (t < nfull) load_tile<THREADS, SUBS>(v, im.rgb + 3 * P * t);
         for (; t < nfull; t += gridDim.x) {
             __syncthreads();                 // previous tile's readers are done
-            stage_tile<THREADS>(sbuf, v);
+            stage_tile<THREADS, SUBS>(sbuf, v);
             __syncthreads();
             const int64_t tn = t + gridDim.x;
-            if (tn < nfull) load_tile<THREADS>(v, im.rgb + 3 * P * tn);   // in flight during compute
+            if (tn < nfull) load_tile<THREADS, SUBS>(v, im.rgb + 3 * P * tn);   // in flight during compute
             const int64_t o = P * t;
-            compute_full<THREADS, OutT, SEL>(sbuf, op, b0 + o, b1 + o, b2 + o, SEL ? sel + o : nullptr);
+            compute_full<THREADS, SUBS, OutT, SEL>(sbuf, op, b0 + o, b1 + o, b2 + o, SEL ? sel + o : nullptr);
         }
         if (nfull < ntiles && blockIdx.x == (unsigned)(nfull % gridDim.x)) {
             __syncthreads();
             const int64_t o = P * nfull;
-            compute_guarded<THREADS, OutT, SEL>(sbuf, im.rgb + 3 * o, (int)(im.width - o), op, b0 + o, b1 + o,
-                                                b2 + o, SEL ? sel + o : nullptr);
+            compute_guarded<THREADS, SUBS, OutT, SEL>(sbuf, im.rgb + 3 * o, (int)(im.width - o), op, b0 + o,
+                                                      b1 + o, b2 + o, SEL ? sel + o : nullptr);
         }
         return;
     }
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         __syncthreads();
-        process_tile<THREADS, OutT, SEL>(im, t, op, sbuf, sel);
+        process_tile<THREADS, OutT, SEL, Op, SUBS>(im, t, op, sbuf, sel);
     }
 }
 

@@ -9,6 +9,18 @@
 
 #include "common.cuh"
 
+namespace mact {
+// Launch shape of the batched kernel: threads per CTA, sub-blocks per tile
+// (tile = threads * 4 * subs pixels) and resident CTAs per SM (0: as many as
+// fit).  Chosen by mact_autotune_batch; the default is 256 x 4 x full.
+struct BatchCfg {
+    int threads = 256;
+    int subs = 4;
+    int ctas_per_sm = 0;
+    int64_t tile_px() const { return (int64_t)threads * 4 * subs; }
+};
+}  // namespace mact
+
 struct mact_ctx {
     int device = 0;
     int num_sms = 0;
@@ -24,6 +36,7 @@ struct mact_ctx {
     cudaEvent_t ev_copy = nullptr;       // staging copy finished
     cudaEvent_t ev_kernel = nullptr;     // last batch kernel finished
     int batch_blocks_per_sm = 0;
+    mact::BatchCfg batch_cfg;            // used by mact_convert_batch and new plans
 
     // LUT interpolation: float4 copy of a large LUT (n > 17), grown on demand
     std::mutex lut_mu;
@@ -46,8 +59,9 @@ mact_status cuda_status(cudaError_t e, const char *what);
 cudaError_t launch_convert(const mact_ctx &h, const ImageDesc &im, cudaStream_t s);
 cudaError_t launch_batch(const mact_ctx &h, const ImageDesc *d_imgs, int32_t count,
                          int64_t total_tiles, unsigned long long *d_counters, int grid,
-                         cudaStream_t s);
-int batch_blocks_per_sm(const mact_ctx &h);
+                         cudaStream_t s, const BatchCfg &cfg = BatchCfg());
+int batch_blocks_per_sm(const mact_ctx &h, const BatchCfg &cfg = BatchCfg());
+bool batch_cfg_supported(const BatchCfg &cfg);
 
 // k_lut.cu
 cudaError_t launch_lut_build(const mact_ctx &h, int n, float *d_lut, cudaStream_t s);
@@ -65,11 +79,12 @@ cudaError_t launch_lab_backward(const mact_ctx &h, const float *x, const float *
 cudaError_t launch_lab_delta_e(const mact_ctx &h, const float *x, const float *tgt, int64_t nb, int64_t hw,
                                float *loss, float *gx, double *partial, cudaStream_t s);
 
-// tile count of an image in the streaming engine
+// tile count of an image descriptor (height x tiles per row)
 int64_t tiles_of(const ImageDesc &im);
 
-// api.cu: argument validation of one image, and its engine descriptor
+// api.cu: argument validation of one image, and its engine descriptor for
+// tiles of tile_px pixels
 mact_status check_image(const mact_image *img);
-ImageDesc make_desc(const mact_image &img);
+ImageDesc make_desc(const mact_image &img, int64_t tile_px = kTile);
 
 }  // namespace mact

@@ -12,7 +12,11 @@
 
 namespace mact {
 
-int64_t tiles_of(const ImageDesc &im) { return tiles_of_t<kThreads>(im); }
+int64_t tiles_of(const ImageDesc &im)
+{
+    if (im.width <= 0 || im.height <= 0) return 0;
+    return im.height * im.tiles_per_row;
+}
 
 using Shape = TileShape<kThreads>;
 
@@ -22,8 +26,10 @@ enum { kNoTable = 0, kTable32 = 1, kTable64 = 2 };
 
 __device__ __forceinline__ void load_table(int kind, const float *gamma, double *sg)
 {
-    if (kind == kTable32) reinterpret_cast<float *>(sg)[threadIdx.x] = gamma[threadIdx.x];
-    else if (kind == kTable64) sg[threadIdx.x] = reinterpret_cast<const double *>(gamma + 256)[threadIdx.x];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        if (kind == kTable32) reinterpret_cast<float *>(sg)[i] = gamma[i];
+        else if (kind == kTable64) sg[i] = reinterpret_cast<const double *>(gamma + 256)[i];
+    }
 }
 
 template <class Op, typename OutT, int TABLE>
@@ -89,30 +95,30 @@ cudaError_t launch_convert(const mact_ctx &h, const ImageDesc &im, cudaStream_t 
 
 // ------------------------------------------------------------ batched form
 
-template <typename OutT, bool EXACT, bool RAT>
+template <typename OutT, bool EXACT, bool RAT, int THREADS, int SUBS>
 __device__ __forceinline__ void batch_tile(const ImageDesc &im, int64_t t, const float *sgam,
                                            const Coeffs &co, uint4 *sbuf)
 {
     if (im.space == MACT_CIELAB) {
         const OpCielab<EXACT, RAT> op{sgam, co};
-        process_tile<kThreads, OutT, false>(im, t, op, sbuf, nullptr);
+        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr);
     } else if (im.space == MACT_HSI) {
         const OpHsi<EXACT> op{co};
-        process_tile<kThreads, OutT, false>(im, t, op, sbuf, nullptr);
+        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr);
     } else {
         const OpSct<EXACT> op{co};
-        process_tile<kThreads, OutT, false>(im, t, op, sbuf, nullptr);
+        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr);
     }
 }
 
-template <bool EXACT, bool RAT>
-__global__ void __launch_bounds__(kThreads)
+template <bool EXACT, bool RAT, int THREADS, int SUBS>
+__global__ void __launch_bounds__(THREADS)
 k_batch(const ImageDesc *__restrict__ imgs, int32_t count, int64_t total,
         unsigned long long *__restrict__ ctr, const __grid_constant__ Coeffs co,
         const float *__restrict__ gamma)
 {
     __shared__ double sgam64[256];
-    __shared__ uint4 sbuf[Shape::vecs];
+    __shared__ uint4 sbuf[TileShape<THREADS, SUBS>::vecs];
     __shared__ long long s_tile;
     __shared__ int s_img;
     load_table((!EXACT && !RAT) ? kTable64 : kTable32, gamma, sgam64);
@@ -137,10 +143,10 @@ k_batch(const ImageDesc *__restrict__ imgs, int32_t count, int64_t total,
         if (t >= total) break;
         const ImageDesc &im = imgs[s_img];
         const int64_t lt = t - im.tile_begin;
-        if (im.dtype == MACT_F16) batch_tile<__half, EXACT, RAT>(im, lt, sgam, co, sbuf);
-        else batch_tile<float, EXACT, RAT>(im, lt, sgam, co, sbuf);
+        if (im.dtype == MACT_F16) batch_tile<__half, EXACT, RAT, THREADS, SUBS>(im, lt, sgam, co, sbuf);
+        else batch_tile<float, EXACT, RAT, THREADS, SUBS>(im, lt, sgam, co, sbuf);
     }
-    // the last CTA out resets the counters for the next launch on the handle
+    // the last CTA out resets the counters for the next launch on the list
     if (threadIdx.x == 0) {
         __threadfence();
         unsigned long long done = atomicAdd(&ctr[1], 1ull);
@@ -151,34 +157,66 @@ k_batch(const ImageDesc *__restrict__ imgs, int32_t count, int64_t total,
     }
 }
 
-template <bool EXACT, bool RAT>
+// Supported launch shapes (threads, sub-blocks): 16 to 32 pixels per thread,
+// tiles of 2048 to 8192 pixels.
+#define MACT_BATCH_SHAPES(X) X(128, 4) X(256, 4) X(512, 4) X(256, 8) X(128, 8)
+
+bool batch_cfg_supported(const BatchCfg &cfg)
+{
+#define MACT_SUPPORTED(T, S) if (cfg.threads == T && cfg.subs == S) return true;
+    MACT_BATCH_SHAPES(MACT_SUPPORTED)
+#undef MACT_SUPPORTED
+    return false;
+}
+
+template <bool EXACT, bool RAT, int THREADS, int SUBS>
 static int occ_batch()
 {
     static int occ = 0;
     if (occ == 0) {
         int o = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch<EXACT, RAT>, kThreads, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch<EXACT, RAT, THREADS, SUBS>,
+                                                                      THREADS, 0);
         occ = (e != cudaSuccess || o <= 0) ? 1 : o;
     }
     return occ;
 }
 
-int batch_blocks_per_sm(const mact_ctx &h)
+template <bool EXACT, bool RAT>
+static int occ_shape(const BatchCfg &cfg)
 {
-    if (h.cfg.exact) return occ_batch<true, true>();
-    return h.co.lab_rational ? occ_batch<false, true>() : occ_batch<false, false>();
+#define MACT_OCC(T, S) if (cfg.threads == T && cfg.subs == S) return occ_batch<EXACT, RAT, T, S>();
+    MACT_BATCH_SHAPES(MACT_OCC)
+#undef MACT_OCC
+    return 1;
+}
+
+int batch_blocks_per_sm(const mact_ctx &h, const BatchCfg &cfg)
+{
+    if (h.cfg.exact) return occ_shape<true, true>(cfg);
+    return h.co.lab_rational ? occ_shape<false, true>(cfg) : occ_shape<false, false>(cfg);
+}
+
+template <bool EXACT, bool RAT>
+static cudaError_t launch_shape(const mact_ctx &h, const ImageDesc *d_imgs, int32_t count, int64_t total,
+                                unsigned long long *d_ctr, int grid, cudaStream_t s, const BatchCfg &cfg)
+{
+#define MACT_LAUNCH(T, S)                                                                               \
+    if (cfg.threads == T && cfg.subs == S) {                                                            \
+        k_batch<EXACT, RAT, T, S><<<grid, T, 0, s>>>(d_imgs, count, total, d_ctr, h.co, h.d_gamma);     \
+        return cudaGetLastError();                                                                      \
+    }
+    MACT_BATCH_SHAPES(MACT_LAUNCH)
+#undef MACT_LAUNCH
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_batch(const mact_ctx &h, const ImageDesc *d_imgs, int32_t count, int64_t total,
-                         unsigned long long *d_ctr, int grid, cudaStream_t s)
+                         unsigned long long *d_ctr, int grid, cudaStream_t s, const BatchCfg &cfg)
 {
-    if (h.cfg.exact)
-        k_batch<true, true><<<grid, kThreads, 0, s>>>(d_imgs, count, total, d_ctr, h.co, h.d_gamma);
-    else if (h.co.lab_rational)
-        k_batch<false, true><<<grid, kThreads, 0, s>>>(d_imgs, count, total, d_ctr, h.co, h.d_gamma);
-    else
-        k_batch<false, false><<<grid, kThreads, 0, s>>>(d_imgs, count, total, d_ctr, h.co, h.d_gamma);
-    return cudaGetLastError();
+    if (h.cfg.exact) return launch_shape<true, true>(h, d_imgs, count, total, d_ctr, grid, s, cfg);
+    if (h.co.lab_rational) return launch_shape<false, true>(h, d_imgs, count, total, d_ctr, grid, s, cfg);
+    return launch_shape<false, false>(h, d_imgs, count, total, d_ctr, grid, s, cfg);
 }
 
 }  // namespace mact

@@ -47,6 +47,11 @@ class Image(ctypes.Structure):
                 ("out", ctypes.c_void_p * 3), ("out_pitch_elems", ctypes.c_int64)]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("px_per_thread", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
+
+
 class ServeStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64), ("pixels", ctypes.c_int64),
@@ -94,6 +99,18 @@ def lib():
         L.mact_serve_destroy.argtypes = [_VP, ctypes.c_double]
         for name in ("mact_serve_create", "mact_serve_submit", "mact_serve_poll", "mact_serve_wait",
                      "mact_serve_cancel", "mact_serve_release", "mact_serve_stats", "mact_serve_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+        L.mact_batch_plan_create.argtypes = [_VP, ctypes.POINTER(Image), ctypes.c_int32, ctypes.POINTER(_VP)]
+        L.mact_batch_plan_launch.argtypes = [_VP, _VP]
+        L.mact_batch_plan_graph_launch.argtypes = [_VP, _VP]
+        L.mact_batch_plan_destroy.argtypes = [_VP]
+        L.mact_autotune_batch.argtypes = [_VP, ctypes.POINTER(Image), ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(TuneEntry), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.mact_set_batch_shape.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.mact_get_batch_shape.argtypes = [_VP] + [ctypes.POINTER(ctypes.c_int32)] * 3
+        for name in ("mact_batch_plan_create", "mact_batch_plan_launch", "mact_batch_plan_graph_launch",
+                     "mact_batch_plan_destroy", "mact_autotune_batch", "mact_set_batch_shape",
+                     "mact_get_batch_shape"):
             getattr(L, name).restype = ctypes.c_int
         L.mact_lab_forward.argtypes = [_VP, _VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP]
         L.mact_lab_backward.argtypes = [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP]
@@ -261,6 +278,76 @@ def mact_lut_interp(h, method, lut, rgb, out=None, sel=False, stream=None):
                                  ctypes.byref(ptrs), _VP(s.data_ptr() if s is not None else 0),
                                  _stream(stream)), "mact_lut_interp")
     return (out, s) if sel else out
+
+
+# ------------------------------------------------ batched plans, autotuner
+
+def _image_array(images, outs):
+    arr = (Image * max(len(images), 1))()
+    for i, ((rgb, space), out) in enumerate(zip(images, outs)):
+        arr[i] = _image(rgb, space, out)
+    return arr
+
+
+def _default_outs(images, dtype):
+    return [torch.empty((3, r.shape[0], r.shape[1]), dtype=dtype, device=r.device) for r, _ in images]
+
+
+class BatchPlan:
+    """A fixed image list with its device work list (mact_batch_plan_t)."""
+
+    def __init__(self, ptr, keep):
+        self.ptr = ptr
+        self._keep = keep
+
+    def launch(self, stream=None):
+        _check(lib().mact_batch_plan_launch(self.ptr, _stream(stream)), "mact_batch_plan_launch")
+
+    def graph_launch(self, stream=None):
+        _check(lib().mact_batch_plan_graph_launch(self.ptr, _stream(stream)), "mact_batch_plan_graph_launch")
+
+    def close(self):
+        if self.ptr:
+            lib().mact_batch_plan_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+def mact_batch_plan_create(h, images, dtype=torch.float32, outs=None):
+    """Plan for a list of (rgb, space); returns (plan, outs)."""
+    outs = _default_outs(images, dtype) if outs is None else outs
+    arr = _image_array(images, outs)
+    p = _VP()
+    _check(lib().mact_batch_plan_create(h.ptr, arr, len(images), ctypes.byref(p)), "mact_batch_plan_create")
+    return BatchPlan(p, (h, images, outs)), outs
+
+
+def mact_autotune_batch(h, images, dtype=torch.float32, outs=None, reps=5):
+    """Time every batch launch shape on these images; the fastest becomes the
+    handle's shape.  Returns (table of dicts, chosen (threads, px/thread, ctas/SM))."""
+    outs = _default_outs(images, dtype) if outs is None else outs
+    arr = _image_array(images, outs)
+    table = (TuneEntry * 32)()
+    n = ctypes.c_int32()
+    _check(lib().mact_autotune_batch(h.ptr, arr, len(images), int(reps), table, 32, ctypes.byref(n)),
+           "mact_autotune_batch")
+    rows = [{k: getattr(table[i], k) for k, _ in TuneEntry._fields_} for i in range(n.value)]
+    return rows, mact_get_batch_shape(h)
+
+
+def mact_set_batch_shape(h, threads, px_per_thread, ctas_per_sm=0):
+    _check(lib().mact_set_batch_shape(h.ptr, threads, px_per_thread, ctas_per_sm), "mact_set_batch_shape")
+
+
+def mact_get_batch_shape(h):
+    v = [ctypes.c_int32() for _ in range(3)]
+    _check(lib().mact_get_batch_shape(h.ptr, *[ctypes.byref(x) for x in v]), "mact_get_batch_shape")
+    return tuple(x.value for x in v)
 
 
 # ------------------------------------------------ differentiable CIELAB
