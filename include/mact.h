@@ -316,6 +316,25 @@ mact_status mact_serve_stats(mact_server_t srv, mact_serve_stats_t *out);
  * wait for in-flight work, and free the server. */
 mact_status mact_serve_destroy(mact_server_t srv, double timeout_ms);
 
+/* ---- transformation error over every 24-bit colour -----------------------
+ * Section "Calculation of the Color Space Transformation Errors" (Tables
+ * tab_cielab, tab_hsi, tab_sct, tab_lut): the average and maximum distance,
+ * over all 2^24 colours, between the transform the library computes (the
+ * production FP32 kernel) and the exact transform evaluated in FP64 on the
+ * device.  The distance is Delta E*ab (Eq. equ_cielab_dist) for CIELAB,
+ * D_HSI (Eq. equ_hsi_dist) for HSI, and for SCT Delta E*ab after the inverse
+ * SCT (Eq. equ_sct_rgb) and conversion to CIELAB.  Colours are generated
+ * from their index (no input).  Blocking; allocates a few KB (and, for
+ * LUTs, an n^3 float4 copy) for the duration of the call. */
+
+/* Error of the handle's transform to space (MACT or exact per the handle). */
+mact_status mact_cube_error(mact_handle h, int32_t space, double *eps_avg, double *eps_max);
+
+/* Error of LUT interpolation (d_lut as for mact_lut_interp) against the
+ * exact CIELAB. */
+mact_status mact_cube_error_lut(mact_handle h, int32_t method, const float *d_lut, int32_t n, double *eps_avg,
+                                double *eps_max);
+
 /* Message for a status code (static storage). */
 const char *mact_strerror(mact_status st);
 

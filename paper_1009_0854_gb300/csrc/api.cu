@@ -445,6 +445,44 @@ mact_status mact_lab_delta_e_loss(mact_handle h, const float *d_x, const float *
     return cuda_status(e, "mact_lab_delta_e_loss");
 }
 
+// ---- transformation error over the RGB cube --------------------------------
+
+mact_status mact_cube_error(mact_handle h, int32_t space, double *eps_avg, double *eps_max)
+{
+    if (!h || !eps_avg || !eps_max) return inval("mact_cube_error: NULL argument");
+    if (space < MACT_CIELAB || space > MACT_SCT) return inval("unknown space");
+    double out[2] = {0.0, 0.0};
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = run_cube_error(*h, space, 0, nullptr, 0, out, s);
+    if (s) cudaStreamDestroy(s);
+    if (e != cudaSuccess) return cuda_status(e, "mact_cube_error");
+    *eps_avg = out[0];
+    *eps_max = out[1];
+    return MACT_OK;
+}
+
+mact_status mact_cube_error_lut(mact_handle h, int32_t method, const float *d_lut, int32_t n, double *eps_avg,
+                                double *eps_max)
+{
+    if (!h || !d_lut || !eps_avg || !eps_max) return inval("mact_cube_error_lut: NULL argument");
+    if (method < MACT_TRILINEAR || method > MACT_TETRA) return inval("unknown interpolation method");
+    if (n < 2 || n > 64) return inval("LUT size must be 2..64");
+    double out[2] = {0.0, 0.0};
+    cudaStream_t s = nullptr;
+    float4 *lut4 = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&lut4, (size_t)n * n * n * sizeof(float4));
+    if (e == cudaSuccess) e = launch_lut_pack4(d_lut, n, lut4, s);
+    if (e == cudaSuccess) e = run_cube_error(*h, 3, method, lut4, n, out, s);
+    if (lut4) cudaFree(lut4);
+    if (s) cudaStreamDestroy(s);
+    if (e != cudaSuccess) return cuda_status(e, "mact_cube_error_lut");
+    *eps_avg = out[0];
+    *eps_max = out[1];
+    return MACT_OK;
+}
+
 const char *mact_strerror(mact_status st)
 {
     switch (st) {

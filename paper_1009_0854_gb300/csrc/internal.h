@@ -79,6 +79,11 @@ cudaError_t launch_lab_backward(const mact_ctx &h, const float *x, const float *
 cudaError_t launch_lab_delta_e(const mact_ctx &h, const float *x, const float *tgt, int64_t nb, int64_t hw,
                                float *loss, float *gx, double *partial, cudaStream_t s);
 
+// k_eps.cu: error statistics over all 2^24 colours (target 0..2: space of the
+// handle's transform; 3: LUT method with float4 nodes)
+cudaError_t run_cube_error(const mact_ctx &h, int target, int method, const float4 *d_lut4, int n,
+                           double out[2], cudaStream_t s);
+
 // tile count of an image descriptor (height x tiles per row)
 int64_t tiles_of(const ImageDesc &im);
 

@@ -112,6 +112,12 @@ def lib():
                      "mact_batch_plan_destroy", "mact_autotune_batch", "mact_set_batch_shape",
                      "mact_get_batch_shape"):
             getattr(L, name).restype = ctypes.c_int
+        L.mact_cube_error.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]
+        L.mact_cube_error_lut.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
+        L.mact_cube_error.restype = ctypes.c_int
+        L.mact_cube_error_lut.restype = ctypes.c_int
         L.mact_lab_forward.argtypes = [_VP, _VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP]
         L.mact_lab_backward.argtypes = [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP]
         L.mact_lab_delta_e_loss.argtypes = [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP]
@@ -278,6 +284,25 @@ def mact_lut_interp(h, method, lut, rgb, out=None, sel=False, stream=None):
                                  ctypes.byref(ptrs), _VP(s.data_ptr() if s is not None else 0),
                                  _stream(stream)), "mact_lut_interp")
     return (out, s) if sel else out
+
+
+# ------------------------------------------------ error over the RGB cube
+
+def mact_cube_error(h, space):
+    """(eps_avg, eps_max) of the handle's transform over all 2^24 colours."""
+    a, m = ctypes.c_double(), ctypes.c_double()
+    sp = SPACES[space] if isinstance(space, str) else int(space)
+    _check(lib().mact_cube_error(h.ptr, sp, ctypes.byref(a), ctypes.byref(m)), "mact_cube_error")
+    return a.value, m.value
+
+
+def mact_cube_error_lut(h, method, lut):
+    """(eps_avg, eps_max) of LUT interpolation over all 2^24 colours."""
+    a, m = ctypes.c_double(), ctypes.c_double()
+    md = METHODS[method] if isinstance(method, str) else int(method)
+    _check(lib().mact_cube_error_lut(h.ptr, md, _VP(lut.data_ptr()), lut.shape[0], ctypes.byref(a),
+                                     ctypes.byref(m)), "mact_cube_error_lut")
+    return a.value, m.value
 
 
 # ------------------------------------------------ batched plans, autotuner
