@@ -16,6 +16,7 @@ so no row reads its input from L2.
 arm) on a bounded sample of the same workload.
 """
 import argparse
+import collections
 import json
 import os
 import statistics
@@ -457,23 +458,24 @@ def run_serve_workload(args):
     trace = synth.serve_trace(rate=2000.0, duration=args.serve_seconds, seed=0)
     maxpx = max(h * w for _, h, w, _, _ in trace)
     pool = torch.from_numpy(synth.request_image(4096, 6144, 2, 7).reshape(-1)).pin_memory()  # 75 MB of content
-    nbuf = 24
-    outs = [torch.empty(3 * maxpx, dtype=torch.float32).pin_memory() for _ in range(nbuf)]
+    arena_elems = 2 << 30                                       # 8 GB of pinned FP32 outputs, used as a ring
+    arena = torch.empty(arena_elems, dtype=torch.float32).pin_memory()
 
-    def req_views(i, hgt, wid):
-        inp = pool[: hgt * wid * 3].view(hgt, wid, 3)
-        out = outs[i % nbuf][: 3 * hgt * wid].view(3, hgt, wid)
-        return inp, out
+    def req_in(hgt, wid):
+        return pool[: hgt * wid * 3].view(hgt, wid, 3)
 
     results = {}
-    # served
+    # served: outputs carved from the ring; the oldest requests are retired
+    # only when the ring wraps onto them
     h = mact.mact_create()
-    srv = mact.mact_serve_create(h, 16 << 30, max_slots=nbuf)
-    pending = {}
+    srv = mact.mact_serve_create(h, 16 << 30, max_slots=128)
+    inflight = collections.deque()    # (start, end, ticket, arrival, submit)
     lat = []
     npx = 0
+    head = 0
 
-    def retire(tk, ta, t_sub):
+    def retire_one():
+        _, _, tk, ta, t_sub = inflight.popleft()
         mact.mact_serve_wait(srv, tk, 600000)
         _, server_ms = mact.mact_serve_poll(srv, tk)
         mact.mact_serve_release(srv, tk)
@@ -482,17 +484,22 @@ def run_serve_workload(args):
     t0 = time.perf_counter()
     for i, (ta, hgt, wid, _, space) in enumerate(trace):
         while time.perf_counter() - t0 < ta:
-            pass
-        slot = i % nbuf
-        if slot in pending:                       # output buffer reuse: wait for its last user
-            retire(*pending.pop(slot))
-        inp, out = req_views(i, hgt, wid)
+            # retire finished requests while waiting for the next arrival
+            if inflight and mact.mact_serve_poll(srv, inflight[0][2])[0]:
+                retire_one()
+        need = 3 * hgt * wid
+        if head + need > arena_elems:
+            head = 0
+        while inflight and any(s0 < head + need and head < e0 for s0, e0, *_ in inflight):
+            retire_one()
+        out = arena[head: head + need].view(3, hgt, wid)
         t_sub = time.perf_counter() - t0
-        tk, _ = mact.mact_serve_submit(srv, inp, space, out=out)
-        pending[slot] = (tk, ta, t_sub)
+        tk, _ = mact.mact_serve_submit(srv, req_in(hgt, wid), space, out=out)
+        inflight.append((head, head + need, tk, ta, t_sub))
+        head += need
         npx += hgt * wid
-    for slot in list(pending):
-        retire(*pending.pop(slot))
+    while inflight:
+        retire_one()
     wall = time.perf_counter() - t0
     st = mact.mact_serve_stats(srv)
     srv.close()
@@ -501,6 +508,10 @@ def run_serve_workload(args):
                          "p99_ms": round(lat[int(0.99 * (len(lat) - 1))], 3), "max_ms": round(lat[-1], 3),
                          "gpix_s": round(npx / wall / 1e9, 3), "batches": st["batches"],
                          "server_p50_ms": round(st["p50_ms"], 3), "server_p99_ms": round(st["p99_ms"], 3)}
+
+    def req_views(i, hgt, wid):
+        return req_in(hgt, wid), arena[: 3 * hgt * wid].view(3, hgt, wid)
+
     # plain: one request at a time, exact libm kernels
     he = mact.mact_create(exact=1)
     dbuf_in = torch.empty(3 * maxpx, dtype=torch.uint8, device=dev)

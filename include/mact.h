@@ -139,9 +139,13 @@ mact_status mact_destroy(mact_handle h);
 mact_status mact_convert(mact_handle h, const mact_image *img, mact_stream stream);
 
 /* Convert count images of any sizes, spaces and dtypes in ONE launch of a
- * persistent kernel that walks a tile work list (the batched form).  The
- * work list lives in a device buffer owned by the handle, grown on demand;
- * calls on one handle from several streams are serialised by the library.
+ * persistent kernel that walks a tile work list (the batched form; Section
+ * "Calculation of the Computational Gain Values" runs the transforms over an
+ * image set).  Each CTA claims 4096-pixel tiles (or the autotuned shape, see
+ * mact_autotune_batch) with an atomic counter, one tile ahead.  The work
+ * list is uploaded from pinned staging into one of 4 device slots owned by
+ * the handle (grown on demand), so up to 4 consecutive calls pipeline; a
+ * slot is reused only after its previous call's copy and kernel are done.
  * Result of each image equals mact_convert of that image. */
 mact_status mact_convert_batch(mact_handle h, const mact_image *imgs, int32_t count,
                                mact_stream stream);

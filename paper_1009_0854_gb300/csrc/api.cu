@@ -256,8 +256,10 @@ mact_status mact_create(const mact_config *cfg, mact_handle *out)
         build_gamma(cfg->rgb, tab.g32, tab.g64);
         e = cudaMemcpy(h->d_gamma, &tab, sizeof(tab), cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_copy, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_kernel, cudaEventDisableTiming);
+    for (auto &sl : h->batch_slots) {
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev_copy, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev_kernel, cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_lut, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_grad, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -274,10 +276,12 @@ mact_status mact_destroy(mact_handle h)
     if (!h) return inval("mact_destroy: NULL handle");
     cudaDeviceSynchronize();
     if (h->d_gamma) cudaFree(h->d_gamma);
-    if (h->d_work) cudaFree(h->d_work);
-    if (h->h_work) cudaFreeHost(h->h_work);
-    if (h->ev_copy) cudaEventDestroy(h->ev_copy);
-    if (h->ev_kernel) cudaEventDestroy(h->ev_kernel);
+    for (auto &sl : h->batch_slots) {
+        if (sl.d_work) cudaFree(sl.d_work);
+        if (sl.h_work) cudaFreeHost(sl.h_work);
+        if (sl.ev_copy) cudaEventDestroy(sl.ev_copy);
+        if (sl.ev_kernel) cudaEventDestroy(sl.ev_kernel);
+    }
     if (h->d_lut4) cudaFree(h->d_lut4);
     if (h->ev_lut) cudaEventDestroy(h->ev_lut);
     if (h->d_partial) cudaFree(h->d_partial);
@@ -307,24 +311,26 @@ mact_status mact_convert_batch(mact_handle h, const mact_image *imgs, int32_t co
     }
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lock(h->batch_mu);
-    // the staging buffer and the device work list are reused: wait for the
-    // previous call's copy (host side) and kernel (stream side) first
-    cudaError_t e = cudaEventSynchronize(h->ev_copy);
+    mact_ctx::BatchSlot &sl = h->batch_slots[h->batch_next];
+    h->batch_next = (h->batch_next + 1) % mact_ctx::kBatchSlots;
+    // this slot's staging buffer and device list were used kBatchSlots calls
+    // ago: wait for that call's copy (host side) and kernel (stream side)
+    cudaError_t e = cudaEventSynchronize(sl.ev_copy);
     if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch: previous copy");
-    if (count > h->work_cap) {
-        e = cudaEventSynchronize(h->ev_kernel);
+    if (count > sl.cap) {
+        e = cudaEventSynchronize(sl.ev_kernel);
         if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch: previous kernel");
         int64_t cap = count < 64 ? 64 : count;
-        if (h->d_work) cudaFree(h->d_work);
-        if (h->h_work) cudaFreeHost(h->h_work);
-        h->d_work = nullptr;
-        h->h_work = nullptr;
-        h->work_cap = 0;
-        e = cudaMalloc(&h->d_work, 256 + cap * sizeof(ImageDesc));
-        if (e == cudaSuccess) e = cudaMemset(h->d_work, 0, 256);
-        if (e == cudaSuccess) e = cudaMallocHost((void **)&h->h_work, cap * sizeof(ImageDesc));
+        if (sl.d_work) cudaFree(sl.d_work);
+        if (sl.h_work) cudaFreeHost(sl.h_work);
+        sl.d_work = nullptr;
+        sl.h_work = nullptr;
+        sl.cap = 0;
+        e = cudaMalloc(&sl.d_work, 256 + cap * sizeof(ImageDesc));
+        if (e == cudaSuccess) e = cudaMemset(sl.d_work, 0, 256);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&sl.h_work, cap * sizeof(ImageDesc));
         if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch: work list allocation");
-        h->work_cap = cap;
+        sl.cap = cap;
     }
     const BatchCfg cfg = h->batch_cfg;
     int64_t total = 0;
@@ -334,21 +340,21 @@ mact_status mact_convert_batch(mact_handle h, const mact_image *imgs, int32_t co
         ImageDesc d = make_desc(imgs[i], cfg.tile_px());
         d.tile_begin = total;
         total += tiles_of(d);
-        h->h_work[n++] = d;
+        sl.h_work[n++] = d;
     }
     if (total == 0) return MACT_OK;
-    unsigned long long *d_ctr = reinterpret_cast<unsigned long long *>(h->d_work);
-    ImageDesc *d_imgs = reinterpret_cast<ImageDesc *>(reinterpret_cast<char *>(h->d_work) + 256);
-    e = cudaStreamWaitEvent(s, h->ev_kernel, 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_imgs, h->h_work, n * sizeof(ImageDesc), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaEventRecord(h->ev_copy, s);
+    unsigned long long *d_ctr = reinterpret_cast<unsigned long long *>(sl.d_work);
+    ImageDesc *d_imgs = reinterpret_cast<ImageDesc *>(reinterpret_cast<char *>(sl.d_work) + 256);
+    e = cudaStreamWaitEvent(s, sl.ev_kernel, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_imgs, sl.h_work, n * sizeof(ImageDesc), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev_copy, s);
     if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch: work list copy");
     int per_sm = batch_blocks_per_sm(*h, cfg);
     if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
     int64_t grid = (int64_t)h->num_sms * per_sm;
     if (grid > total) grid = total;
     e = launch_batch(*h, d_imgs, n, total, d_ctr, (int)grid, s, cfg);
-    if (e == cudaSuccess) e = cudaEventRecord(h->ev_kernel, s);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev_kernel, s);
     return cuda_status(e, "mact_convert_batch launch");
 }
 

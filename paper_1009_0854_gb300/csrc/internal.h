@@ -28,14 +28,20 @@ struct mact_ctx {
     mact::Coeffs co{};
     float *d_gamma = nullptr;            // 256 FP32 then 256 FP64 entries (Eq. equ_rgb_lin of each code)
 
-    // batched form: work list (image descriptors) and the tile counters
+    // batched form: a ring of work-list slots, so consecutive calls pipeline
+    // (a slot is reused only after the call that last used it has copied its
+    // list and finished its kernel)
+    struct BatchSlot {
+        mact::ImageDesc *h_work = nullptr;   // pinned staging
+        void *d_work = nullptr;              // [256 B: 2 x u64 counters][ImageDesc x cap]
+        int64_t cap = 0;
+        cudaEvent_t ev_copy = nullptr;       // staging copy finished
+        cudaEvent_t ev_kernel = nullptr;     // batch kernel finished
+    };
+    static constexpr int kBatchSlots = 4;
     std::mutex batch_mu;
-    mact::ImageDesc *h_work = nullptr;   // pinned staging
-    void *d_work = nullptr;              // [2 x u64 counters][ImageDesc x cap]
-    int64_t work_cap = 0;
-    cudaEvent_t ev_copy = nullptr;       // staging copy finished
-    cudaEvent_t ev_kernel = nullptr;     // last batch kernel finished
-    int batch_blocks_per_sm = 0;
+    BatchSlot batch_slots[kBatchSlots];
+    int batch_next = 0;
     mact::BatchCfg batch_cfg;            // used by mact_convert_batch and new plans
 
     // LUT interpolation: float4 copy of a large LUT (n > 17), grown on demand
