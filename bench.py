@@ -50,30 +50,42 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_table():
-    """Per-launch DRAM bytes from the committed ncu summary, keyed by row,
-    with the source hash the capture was taken on (None if stale/absent)."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
-    out = {}
-    if not os.path.exists(path):
-        return out
-    cur = source_hash()
-    for line in open(path):
-        line = line.split("#", 1)[0].split()
-        if len(line) == 3 and line[2] == cur:
-            out[line[0]] = float(line[1])
-    return out
+KERNEL_FILES = {
+    "convert": ("common.cuh", "engine.cuh", "pixel.cuh", "k_convert.cu"),
+    "lut": ("common.cuh", "engine.cuh", "k_lut.cu"),
+}
 
 
-def source_hash():
+def kernel_group(row):
+    return "lut" if row.startswith("lut") else "convert"
+
+
+def source_hash(group):
+    """Hash of the source files that define a row's kernel: a recorded DRAM
+    traffic figure is only reported while these are unchanged."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1009_0854_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in KERNEL_FILES[group]:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode())
             h.update(fh.read())
     return h.hexdigest()[:12]
+
+
+def traffic_table():
+    """Per-launch DRAM bytes (read + write) from the committed ncu summary
+    profiles/traffic.txt, for rows whose kernel sources still hash the same."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    out = {}
+    if not os.path.exists(path):
+        return out
+    cur = {g: source_hash(g) for g in KERNEL_FILES}
+    for line in open(path):
+        line = line.split("#", 1)[0].split()
+        if len(line) == 3 and line[2] == cur[kernel_group(line[0])]:
+            out[line[0]] = float(line[1])
+    return out
 
 
 class ClockSampler:
@@ -124,6 +136,18 @@ class ClockSampler:
         reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows)}
+
+
+def max_over_ranks(value, device=None):
+    """The largest value over all ranks (the slowest replica sets the step
+    time); the identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_env():
@@ -201,11 +225,7 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(t0.elapsed_time(t1), dev)
     launches = args.steps * len(ROWS)
 
     row_ms = {name: statistics.mean(a.elapsed_time(b) for a, b in ev[name]) for name in ev}
@@ -252,11 +272,7 @@ def run_gpu(args):
             e2e_step()
         b.record(stream)
         torch.cuda.synchronize()
-        ems = a.elapsed_time(b) / k
-        if world > 1:
-            tt = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = float(tt.item())
+        ems = max_over_ranks(a.elapsed_time(b) / k, dev)
         e2e = {"value": round(world * len(ROWS) * PIX / (ems * 1e-3) / 1e9, 3), "unit": "Gpix/s",
                "h2d_bytes_per_step": 3 * PIX, "d2h_bytes_per_step": len(ROWS) * 12 * PIX,
                "ms_per_step": round(ems, 4)}
@@ -447,96 +463,183 @@ def run_grad_workload(args):
     print(json.dumps({"workload": "grad: fused mean-DeltaE loss + backward, 64x3x512x512 FP32", "rows": rows}))
 
 
+def run_lut_workload(args):
+    """Standard vs caching LUT layout, 4 methods x {9, 17, 33}^3, on the
+    2^24-colour cube (coherent) and on i.i.d. uniform noise (incoherent)."""
+    import numpy as np
+    import torch
+    from paper_1009_0854_gb300 import mact, synth
+    dev = torch.device("cuda", 0)
+    h = mact.mact_create()
+    inputs = {"cube": torch.from_numpy(synth.rgb_cube()).to(dev),
+              "noise": torch.from_numpy(np.random.default_rng(0).integers(0, 256, size=(4096, 4096, 3),
+                                                                        dtype=np.uint8)).to(dev)}
+    out = torch.empty((3, PIX), device=dev)
+    hbm, _ = peaks()
+    rows = {}
+    for n in (9, 17, 33):
+        lut = mact.mact_lut_build(h, n, device=dev)
+        cache = mact.mact_lut_cache_build(h, lut)
+        for name, x in inputs.items():
+            xs = [x.clone() for _ in range(4)]
+            for m in ("trilinear", "prism", "pyramid", "tetra"):
+                for layout in ("standard", "caching"):
+                    if layout == "standard":
+                        fn = lambda v: mact.mact_lut_interp(h, m, lut, v, out=out)
+                    else:
+                        fn = lambda v: mact.mact_lut_interp_cached(h, m, cache, n, v, out=out)
+                    for i in range(3):
+                        fn(xs[i % 4])
+                    torch.cuda.synchronize()
+                    a, b = _events(torch)
+                    a.record()
+                    for i in range(args.steps):
+                        fn(xs[i % 4])
+                    b.record()
+                    torch.cuda.synchronize()
+                    ms = a.elapsed_time(b) / args.steps
+                    rows["%s_lut%d_%s_%s" % (name, n, m, layout)] = {
+                        "gpix_s": round(PIX / ms / 1e6, 1), "hbm_frac": round(PIX * 15 / (ms * 1e-3) / 1e9 / hbm, 4)}
+    print(json.dumps({"workload": "lut: standard vs caching layout, cube and uniform noise, 2^24 px", "rows": rows}))
+
+
+class PinnedPool:
+    """Pinned host buffers for request outputs, by power-of-two size class,
+    reused last-in-first-out (as a server recycles response buffers), with a
+    cap on the total pinned bytes."""
+
+    def __init__(self, torch, cap_bytes=10 << 30):
+        self.torch = torch
+        self.free = collections.defaultdict(list)
+        self.cap = cap_bytes
+        self.total = 0
+
+    @staticmethod
+    def cls(n):
+        return max(1 << 20, 1 << (int(n) - 1).bit_length())
+
+    def _new(self, c):
+        self.total += c
+        return self.torch.empty(c // 4, dtype=self.torch.float32).pin_memory()
+
+    def take(self, n, reclaim=None):
+        """A buffer of at least n bytes; when the cap is reached, reclaim()
+        (which must return one buffer to the pool) is called until one of
+        this class is free or room is made."""
+        c = self.cls(n)
+        while True:
+            if self.free[c]:
+                return self.free[c].pop()
+            if self.total + c <= self.cap:
+                return self._new(c)
+            freed = False
+            for oc in sorted(self.free):           # drop idle buffers of other classes
+                if oc != c and self.free[oc]:
+                    self.free[oc].pop()
+                    self.total -= oc
+                    freed = True
+                    break
+            if not freed:
+                if reclaim is None:
+                    raise MemoryError("pinned pool exhausted")
+                reclaim()
+
+    def give(self, buf):
+        self.free[buf.numel() * 4].append(buf)
+
+    def warm(self, sizes, per_class=6):
+        want = collections.Counter(self.cls(n) for n in sizes)
+        for c in sorted(want):
+            for _ in range(min(want[c], per_class if c <= (64 << 20) else 2)):
+                if self.total + c <= self.cap:
+                    self.free[c].append(self._new(c))
+
+
 def run_serve_workload(args):
     """Poisson arrivals (2000/s) of 0.1-24 Mpx images, 50/25/25% CIELAB/HSI/SCT,
-    pinned host input and output, through the continuous-batching server
-    (MACT, 16 GB staging budget) and through the plain path (one request at a
-    time: H2D, exact-libm kernel, D2H)."""
+    pinned host input and output (output buffers from a LIFO pool shared by
+    both paths), through the continuous-batching server (MACT, 16 GB staging
+    budget) and through the plain path (one request at a time: H2D,
+    exact-libm kernel, D2H).  Latency counts from the trace's arrival time."""
     import torch
     from paper_1009_0854_gb300 import mact, synth
     dev = torch.device("cuda", 0)
     trace = synth.serve_trace(rate=2000.0, duration=args.serve_seconds, seed=0)
     maxpx = max(h * w for _, h, w, _, _ in trace)
-    pool = torch.from_numpy(synth.request_image(4096, 6144, 2, 7).reshape(-1)).pin_memory()  # 75 MB of content
-    arena_elems = 2 << 30                                       # 8 GB of pinned FP32 outputs, used as a ring
-    arena = torch.empty(arena_elems, dtype=torch.float32).pin_memory()
+    pool_in = torch.from_numpy(synth.request_image(4096, 6144, 2, 7).reshape(-1)).pin_memory()  # 75 MB
+    outs = PinnedPool(torch)
+    outs.warm([12 * h * w for _, h, w, _, _ in trace])
 
     def req_in(hgt, wid):
-        return pool[: hgt * wid * 3].view(hgt, wid, 3)
+        return pool_in[: hgt * wid * 3].view(hgt, wid, 3)
+
+    def summary(lat, npx, wall, extra=None):
+        lat = sorted(lat)
+        d = {"requests": len(lat), "p50_ms": round(lat[len(lat) // 2], 3),
+             "p99_ms": round(lat[int(0.99 * (len(lat) - 1))], 3), "max_ms": round(lat[-1], 3),
+             "gpix_s": round(npx / wall / 1e9, 3)}
+        d.update(extra or {})
+        return d
 
     results = {}
-    # served: outputs carved from the ring; the oldest requests are retired
-    # only when the ring wraps onto them
+    # served
     h = mact.mact_create()
     srv = mact.mact_serve_create(h, 16 << 30, max_slots=128)
-    inflight = collections.deque()    # (start, end, ticket, arrival, submit)
+    inflight = collections.deque()    # (ticket, arrival, submit, buffer)
     lat = []
     npx = 0
-    head = 0
 
     def retire_one():
-        _, _, tk, ta, t_sub = inflight.popleft()
+        tk, ta, t_sub, buf = inflight.popleft()
         mact.mact_serve_wait(srv, tk, 600000)
         _, server_ms = mact.mact_serve_poll(srv, tk)
         mact.mact_serve_release(srv, tk)
-        lat.append((t_sub - ta) * 1e3 + server_ms)     # from arrival: queueing in the driver counts
+        outs.give(buf)
+        lat.append((t_sub - ta) * 1e3 + server_ms)
 
     t0 = time.perf_counter()
-    for i, (ta, hgt, wid, _, space) in enumerate(trace):
+    for ta, hgt, wid, _, space in trace:
         while time.perf_counter() - t0 < ta:
-            # retire finished requests while waiting for the next arrival
-            if inflight and mact.mact_serve_poll(srv, inflight[0][2])[0]:
+            if inflight and mact.mact_serve_poll(srv, inflight[0][0])[0]:
                 retire_one()
-        need = 3 * hgt * wid
-        if head + need > arena_elems:
-            head = 0
-        while inflight and any(s0 < head + need and head < e0 for s0, e0, *_ in inflight):
-            retire_one()
-        out = arena[head: head + need].view(3, hgt, wid)
+            else:
+                time.sleep(5e-5)
+        buf = outs.take(12 * hgt * wid, reclaim=retire_one)
         t_sub = time.perf_counter() - t0
-        tk, _ = mact.mact_serve_submit(srv, req_in(hgt, wid), space, out=out)
-        inflight.append((head, head + need, tk, ta, t_sub))
-        head += need
+        tk, _ = mact.mact_serve_submit(srv, req_in(hgt, wid), space, out=buf[: 3 * hgt * wid].view(3, hgt, wid))
+        inflight.append((tk, ta, t_sub, buf))
         npx += hgt * wid
     while inflight:
         retire_one()
     wall = time.perf_counter() - t0
     st = mact.mact_serve_stats(srv)
     srv.close()
-    lat.sort()
-    results["served"] = {"requests": len(trace), "p50_ms": round(lat[len(lat) // 2], 3),
-                         "p99_ms": round(lat[int(0.99 * (len(lat) - 1))], 3), "max_ms": round(lat[-1], 3),
-                         "gpix_s": round(npx / wall / 1e9, 3), "batches": st["batches"],
-                         "server_p50_ms": round(st["p50_ms"], 3), "server_p99_ms": round(st["p99_ms"], 3)}
-
-    def req_views(i, hgt, wid):
-        return req_in(hgt, wid), arena[: 3 * hgt * wid].view(3, hgt, wid)
-
+    results["served"] = summary(lat, npx, wall, {"batches": st["batches"], "server_p50_ms": round(st["p50_ms"], 3),
+                                                 "server_p99_ms": round(st["p99_ms"], 3)})
     # plain: one request at a time, exact libm kernels
     he = mact.mact_create(exact=1)
     dbuf_in = torch.empty(3 * maxpx, dtype=torch.uint8, device=dev)
     dbuf_out = torch.empty(3 * maxpx, dtype=torch.float32, device=dev)
     s = torch.cuda.current_stream()
     lat = []
-    t0 = time.perf_counter()
     npx = 0
-    for i, (ta, hgt, wid, _, space) in enumerate(trace):
+    t0 = time.perf_counter()
+    for ta, hgt, wid, _, space in trace:
         while time.perf_counter() - t0 < ta:
             pass
-        inp, out = req_views(i, hgt, wid)
+        inp = req_in(hgt, wid)
+        buf = outs.take(12 * hgt * wid)
         din = dbuf_in[: hgt * wid * 3].view(hgt, wid, 3)
         dout = dbuf_out[: 3 * hgt * wid].view(3, hgt, wid)
         din.copy_(inp, non_blocking=True)
         mact.mact_convert(he, din, space, out=dout, stream=s)
-        out.copy_(dout, non_blocking=True)
+        buf[: 3 * hgt * wid].view(3, hgt, wid).copy_(dout, non_blocking=True)
         s.synchronize()
+        outs.give(buf)
         lat.append((time.perf_counter() - t0 - ta) * 1e3)
         npx += hgt * wid
     wall = time.perf_counter() - t0
-    lat.sort()
-    results["plain_exact_per_image"] = {"requests": len(trace), "p50_ms": round(lat[len(lat) // 2], 3),
-                                        "p99_ms": round(lat[int(0.99 * (len(lat) - 1))], 3),
-                                        "max_ms": round(lat[-1], 3), "gpix_s": round(npx / wall / 1e9, 3)}
+    results["plain_exact_per_image"] = summary(lat, npx, wall)
     print(json.dumps({"workload": "serve: Poisson 2000 req/s for %g s, 0.1-24 Mpx, pinned host buffers"
                       % args.serve_seconds, "rows": results}))
 
@@ -551,7 +654,7 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=1 << 22)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cube", choices=["cube", "batch", "serve", "grad"],
+    ap.add_argument("--workload", default="cube", choices=["cube", "batch", "serve", "grad", "lut"],
                     help="cube: the default step; the others measure the batched, served and "
                          "differentiable forms on their own workloads")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -565,6 +668,8 @@ def main():
         run_serve_workload(args)
     elif args.workload == "grad":
         run_grad_workload(args)
+    elif args.workload == "lut":
+        run_lut_workload(args)
     else:
         run_gpu(args)
 

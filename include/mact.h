@@ -142,7 +142,7 @@ mact_status mact_convert(mact_handle h, const mact_image *img, mact_stream strea
  * persistent kernel that walks a tile work list (the batched form; Section
  * "Calculation of the Computational Gain Values" runs the transforms over an
  * image set).  Each CTA claims 4096-pixel tiles (or the autotuned shape, see
- * mact_autotune_batch) with an atomic counter, one tile ahead.  The work
+ * mact_autotune_batch) with an atomic counter.  The work
  * list is uploaded from pinned staging into one of 4 device slots owned by
  * the handle (grown on demand), so up to 4 consecutive calls pipeline; a
  * slot is reused only after its previous call's copy and kernel are done.
@@ -338,6 +338,24 @@ mact_status mact_cube_error(mact_handle h, int32_t space, double *eps_avg, doubl
  * exact CIELAB. */
 mact_status mact_cube_error_lut(mact_handle h, int32_t method, const float *d_lut, int32_t n, double *eps_avg,
                                 double *eps_max);
+
+/* ---- "caching" LUT layout --------------------------------------------
+ * Section "Comparison with 3D Lookup Table Interpolation Methods": besides
+ * the standard form, the paper implements each LUT method in a "caching"
+ * form that precomputes the differences between neighbouring lattice nodes
+ * and stores them with each node.  Here each cell (lower corner (i, j, k),
+ * 0 <= i, j, k <= n-2) gets one 128-byte record of 8 float4: c000 and the
+ * seven differences c_xyz - c000 (slot x*4 + y*2 + z; x = R, y = G, z = B;
+ * the fourth lane unused), so a pixel's neighbourhood is one cache line.
+ * d_cache must hold (n-1)^3 * 32 floats and be 16-byte aligned. */
+mact_status mact_lut_cache_build(mact_handle h, const float *d_lut, int32_t n, float *d_cache, mact_stream stream);
+
+/* Interpolation from the caching layout: same methods, the same cells,
+ * simplices and selection ids as mact_lut_interp, the same values up to FP32
+ * rounding (c000 + weighted differences). */
+mact_status mact_lut_interp_cached(mact_handle h, int32_t method, const float *d_cache, int32_t n,
+                                   const uint8_t *d_rgb, int64_t npix, float *const d_out[3], int32_t *d_sel,
+                                   mact_stream stream);
 
 /* Message for a status code (static storage). */
 const char *mact_strerror(mact_status st);

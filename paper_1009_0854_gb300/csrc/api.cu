@@ -489,6 +489,32 @@ mact_status mact_cube_error_lut(mact_handle h, int32_t method, const float *d_lu
     return MACT_OK;
 }
 
+mact_status mact_lut_cache_build(mact_handle h, const float *d_lut, int32_t n, float *d_cache, mact_stream stream)
+{
+    if (!h) return inval("mact_lut_cache_build: NULL handle");
+    if (n < 2 || n > 64) return inval("LUT size must be 2..64");
+    if (!d_lut || !d_cache) return inval("NULL pointer");
+    if ((reinterpret_cast<uintptr_t>(d_cache) & 15) != 0) return inval("d_cache must be 16-byte aligned");
+    return cuda_status(launch_lut_cache_build(d_lut, n, reinterpret_cast<float4 *>(d_cache), (cudaStream_t)stream),
+                       "mact_lut_cache_build");
+}
+
+mact_status mact_lut_interp_cached(mact_handle h, int32_t method, const float *d_cache, int32_t n,
+                                   const uint8_t *d_rgb, int64_t npix, float *const d_out[3], int32_t *d_sel,
+                                   mact_stream stream)
+{
+    if (!h) return inval("mact_lut_interp_cached: NULL handle");
+    if (method < MACT_TRILINEAR || method > MACT_TETRA) return inval("unknown interpolation method");
+    if (n < 2 || n > 64) return inval("LUT size must be 2..64");
+    if (npix < 0 || npix > (int64_t(1) << 42)) return inval("pixel count out of range");
+    if (npix == 0) return MACT_OK;
+    if (!d_cache || !d_rgb || !d_out || !d_out[0] || !d_out[1] || !d_out[2]) return inval("NULL pointer");
+    if ((reinterpret_cast<uintptr_t>(d_cache) & 15) != 0) return inval("d_cache must be 16-byte aligned");
+    return cuda_status(launch_lut_interp_cached(*h, method, reinterpret_cast<const float4 *>(d_cache), n, d_rgb,
+                                                npix, d_out, d_sel, (cudaStream_t)stream),
+                       "mact_lut_interp_cached");
+}
+
 const char *mact_strerror(mact_status st)
 {
     switch (st) {

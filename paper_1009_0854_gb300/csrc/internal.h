@@ -75,6 +75,10 @@ cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut,
                               const uint8_t *d_rgb, int64_t npix, float *const out[3],
                               int32_t *d_sel, const float4 *d_lut4, cudaStream_t s);
 cudaError_t launch_lut_pack4(const float *d_lut, int n, float4 *d_lut4, cudaStream_t s);
+cudaError_t launch_lut_cache_build(const float *d_lut, int n, float4 *d_cache, cudaStream_t s);
+cudaError_t launch_lut_interp_cached(const mact_ctx &h, int method, const float4 *d_cache, int n,
+                                     const uint8_t *d_rgb, int64_t npix, float *const out[3], int32_t *d_sel,
+                                     cudaStream_t s);
 bool lut_needs_pack(int n);
 
 // k_grad.cu

@@ -95,129 +95,56 @@ cudaError_t launch_convert(const mact_ctx &h, const ImageDesc &im, cudaStream_t 
 
 // ------------------------------------------------------------ batched form
 
-// Where tile t of image im lives, and whether it takes the vector path.
-struct TileRef {
-    const uint8_t *in = nullptr;
-    int64_t off = 0;      // output element offset of the tile
-    int cnt = 0;          // pixels in the tile
-    bool fast = false;    // full tile, every pointer aligned for vectors
-};
-
-template <int P>
-__device__ __forceinline__ TileRef tile_ref(const ImageDesc &im, int64_t t)
-{
-    TileRef r;
-    const uint32_t tpr = (uint32_t)im.tiles_per_row;
-    const uint32_t tt = (uint32_t)t;
-    const uint32_t row = tt / tpr;
-    const int64_t x0 = (int64_t)(tt - row * tpr) * P;
-    const int64_t rem_px = im.width - x0;
-    r.cnt = rem_px < P ? (int)rem_px : P;
-    r.in = im.rgb + (int64_t)row * im.pitch + 3 * x0;
-    r.off = (int64_t)row * im.opitch + x0;
-    const size_t es = im.dtype == MACT_F16 ? 2 : 4;
-    const uintptr_t omask = es == 4 ? 15 : 7;
-    const uintptr_t oa = (reinterpret_cast<uintptr_t>(im.out[0]) + r.off * es) |
-                         (reinterpret_cast<uintptr_t>(im.out[1]) + r.off * es) |
-                         (reinterpret_cast<uintptr_t>(im.out[2]) + r.off * es);
-    r.fast = r.cnt == P && ((reinterpret_cast<uintptr_t>(r.in) & 15) == 0) && ((oa & omask) == 0);
-    return r;
-}
-
 template <typename OutT, bool EXACT, bool RAT, int THREADS, int SUBS>
-__device__ __forceinline__ void batch_compute(const ImageDesc &im, const TileRef &r, const float *sgam,
-                                              const Coeffs &co, uint4 *sbuf)
+__device__ __forceinline__ void batch_tile(const ImageDesc &im, int64_t t, const float *sgam,
+                                           const Coeffs &co, uint4 *sbuf)
 {
-    OutT *o0 = reinterpret_cast<OutT *>(im.out[0]) + r.off;
-    OutT *o1 = reinterpret_cast<OutT *>(im.out[1]) + r.off;
-    OutT *o2 = reinterpret_cast<OutT *>(im.out[2]) + r.off;
     if (im.space == MACT_CIELAB) {
         const OpCielab<EXACT, RAT> op{sgam, co};
-        if (r.fast) compute_full<THREADS, SUBS, OutT, false>(sbuf, op, o0, o1, o2, nullptr);
-        else compute_guarded<THREADS, SUBS, OutT, false>(sbuf, r.in, r.cnt, op, o0, o1, o2, nullptr);
+        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr);
     } else if (im.space == MACT_HSI) {
         const OpHsi<EXACT> op{co};
-        if (r.fast) compute_full<THREADS, SUBS, OutT, false>(sbuf, op, o0, o1, o2, nullptr);
-        else compute_guarded<THREADS, SUBS, OutT, false>(sbuf, r.in, r.cnt, op, o0, o1, o2, nullptr);
+        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr);
     } else {
         const OpSct<EXACT> op{co};
-        if (r.fast) compute_full<THREADS, SUBS, OutT, false>(sbuf, op, o0, o1, o2, nullptr);
-        else compute_guarded<THREADS, SUBS, OutT, false>(sbuf, r.in, r.cnt, op, o0, o1, o2, nullptr);
+        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr);
     }
 }
 
-__device__ __forceinline__ int find_image(const ImageDesc *__restrict__ imgs, int count, long long t)
-{
-    // last image whose first tile is <= t (the list is sorted by tile_begin)
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (imgs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Persistent work-list kernel.  Each CTA claims tiles with an atomic
-// counter, one tile ahead: while it computes tile i from shared memory, the
-// 16-byte vectors of tile i+1 (already claimed) are in flight into
-// registers.  Tiles that are partial or misaligned take the guarded path.
 template <bool EXACT, bool RAT, int THREADS, int SUBS>
 __global__ void __launch_bounds__(THREADS)
 k_batch(const ImageDesc *__restrict__ imgs, int32_t count, int64_t total,
         unsigned long long *__restrict__ ctr, const __grid_constant__ Coeffs co,
         const float *__restrict__ gamma)
 {
-    constexpr int P = TileShape<THREADS, SUBS>::px;
     __shared__ double sgam64[256];
     __shared__ uint4 sbuf[TileShape<THREADS, SUBS>::vecs];
-    __shared__ long long s_tile[2];
-    __shared__ int s_img[2];
+    __shared__ long long s_tile;
+    __shared__ int s_img;
     load_table((!EXACT && !RAT) ? kTable64 : kTable32, gamma, sgam64);
     const float *sgam = reinterpret_cast<const float *>(sgam64);
-    if (threadIdx.x == 0) {
-        const long long t = (long long)atomicAdd(&ctr[0], 1ull);
-        s_tile[0] = t;
-        s_img[0] = t < total ? find_image(imgs, count, t) : 0;
-    }
-    __syncthreads();
-    int cur = 0;
-    long long t = s_tile[0];
-    int img = s_img[0];
-    TileRef ref;
-    uint4 v[TileShape<THREADS, SUBS>::vpt];
-    if (t < total) {
-        ref = tile_ref<P>(imgs[img], t - imgs[img].tile_begin);
-        if (ref.fast) load_tile<THREADS, SUBS>(v, ref.in);
-    }
-    while (t < total) {
-        const int nxt = cur ^ 1;
+    for (;;) {
+        __syncthreads();   // previous tile finished with sbuf / s_tile
         if (threadIdx.x == 0) {
-            const long long tn = (long long)atomicAdd(&ctr[0], 1ull);
-            s_tile[nxt] = tn;
-            s_img[nxt] = tn < total ? find_image(imgs, count, tn) : 0;
+            long long t = (long long)atomicAdd(&ctr[0], 1ull);
+            s_tile = t;
+            if (t < total) {
+                // last image whose first tile is <= t (list sorted by tile_begin)
+                int lo = 0, hi = count - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (imgs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+                }
+                s_img = lo;
+            }
         }
-        __syncthreads();   // (A) s_tile[nxt] visible; the previous tile is done with sbuf
-        const long long tn = s_tile[nxt];
-        const int imn = s_img[nxt];
-        TileRef nref;
-        if (tn < total) nref = tile_ref<P>(imgs[imn], tn - imgs[imn].tile_begin);
-        const ImageDesc &im = imgs[img];
-        if (ref.fast) {
-            stage_tile<THREADS, SUBS>(sbuf, v);
-            __syncthreads();   // (B) staged tile visible; every thread has read s_tile[nxt]
-            if (nref.fast) load_tile<THREADS, SUBS>(v, nref.in);   // in flight during compute
-            if (im.dtype == MACT_F16) batch_compute<__half, EXACT, RAT, THREADS, SUBS>(im, ref, sgam, co, sbuf);
-            else batch_compute<float, EXACT, RAT, THREADS, SUBS>(im, ref, sgam, co, sbuf);
-        } else {
-            // guarded: byte copy, barrier (every thread has read s_tile[nxt]), compute
-            if (im.dtype == MACT_F16) batch_compute<__half, EXACT, RAT, THREADS, SUBS>(im, ref, sgam, co, sbuf);
-            else batch_compute<float, EXACT, RAT, THREADS, SUBS>(im, ref, sgam, co, sbuf);
-            if (nref.fast) load_tile<THREADS, SUBS>(v, nref.in);
-        }
-        t = tn;
-        img = imn;
-        ref = nref;
-        cur = nxt;
+        __syncthreads();
+        const long long t = s_tile;
+        if (t >= total) break;
+        const ImageDesc &im = imgs[s_img];
+        const int64_t lt = t - im.tile_begin;
+        if (im.dtype == MACT_F16) batch_tile<__half, EXACT, RAT, THREADS, SUBS>(im, lt, sgam, co, sbuf);
+        else batch_tile<float, EXACT, RAT, THREADS, SUBS>(im, lt, sgam, co, sbuf);
     }
     // the last CTA out resets the counters for the next launch on the list
     if (threadIdx.x == 0) {

@@ -69,6 +69,36 @@ __global__ void k_lut_pack4(const float *__restrict__ lut, int nodes, float4 *__
     if (i < nodes) out[i] = make_float4(lut[3 * i], lut[3 * i + 1], lut[3 * i + 2], 0.0f);
 }
 
+// "Caching" layout (the paper's second implementation of each LUT method:
+// the differences between neighbouring lattice nodes are precomputed and
+// stored with each node): one 128-byte record per cell (i, j, k), i.e. per
+// lower corner, holding c000 and the seven differences c_xyz - c000 as
+// float4, slot x*4 + y*2 + z (x = R, y = G, z = B offset).  A pixel reads its
+// whole neighbourhood from one cache line.
+__global__ void k_lut_cache_build(const float *__restrict__ lut, int n, float4 *__restrict__ cache)
+{
+    const int m = n - 1;
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= m * m * m) return;
+    const int k = cell % m, j = (cell / m) % m, i = cell / (m * m);
+    const int64_t b0 = ((int64_t)(i * n + j) * n + k) * 3;
+    float4 *rec = cache + (int64_t)cell * 8;
+    const float c0x = lut[b0], c0y = lut[b0 + 1], c0z = lut[b0 + 2];
+    rec[0] = make_float4(c0x, c0y, c0z, 0.0f);
+    for (int slot = 1; slot < 8; ++slot) {
+        const int x = slot >> 2, y = (slot >> 1) & 1, z = slot & 1;
+        const int64_t o = ((int64_t)((i + x) * n + (j + y)) * n + (k + z)) * 3;
+        rec[slot] = make_float4(lut[o] - c0x, lut[o + 1] - c0y, lut[o + 2] - c0z, 0.0f);
+    }
+}
+
+cudaError_t launch_lut_cache_build(const float *d_lut, int n, float4 *d_cache, cudaStream_t s)
+{
+    const int cells = (n - 1) * (n - 1) * (n - 1);
+    k_lut_cache_build<<<(cells + 255) / 256, 256, 0, s>>>(d_lut, n, d_cache);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------- interpolation
 
 // Per-code extraction table entry: node offset along the axis and fraction.
@@ -114,11 +144,40 @@ struct Strides {
     __device__ __forceinline__ int g() const { return N > 0 ? N : n; }
 };
 
-template <int METHOD, int N, bool SMEM>
+// Nodes each method reads from its cell.
+template <int METHOD>
+struct NodeCount {
+    static constexpr int K = METHOD == MACT_TRILINEAR ? 8 : METHOD == MACT_PRISM ? 6 : METHOD == MACT_PYRAMID ? 5 : 4;
+};
+
+// Extraction result of one pixel: the cell, the simplex, the offsets of the
+// nodes to read (relative to the cell's lower corner) and the three weights
+// the interpolation formula uses.
+template <int METHOD>
+struct Sel {
+    int base;     // lower-corner node index
+    int rec;      // cell record index (caching layout)
+    int simplex;
+    int off[NodeCount<METHOD>::K];
+    float w0, w1, w2;
+};
+
+// CACHED: nodes come from the per-cell records of the caching layout (base
+// is still the lower-corner node index, for the selection id; rec is the
+// cell's record index; node offsets become record slots and the value is
+// c000 + the interpolation of the differences).
+template <int METHOD, int N, bool SMEM, bool CACHED = false>
 struct OpLut {
-    const float4 *lut;        // shared or global float4 nodes
+    // Per-pixel evaluation.  (A quad() form that reuses a cell's nodes across
+    // the thread's 4 pixels is kept, but disabled: the predicated reloads
+    // and the live node registers cost more than the gathers they save on
+    // every input measured -- coherent cube, smooth and noisy images.)
+    static constexpr bool kQuad = false;
+    static constexpr int K = NodeCount<METHOD>::K;
+    const float4 *lut;        // shared or global float4 nodes, or cell records
     const AxisEntry *tab;     // shared extraction table
     Strides<N> st;
+
     __device__ __forceinline__ static void locate(uint32_t v, int n, int &idx, float &f)
     {
         const int s = (int)v * (n - 1);
@@ -130,15 +189,15 @@ struct OpLut {
         f = (float)rem * (1.0f / 255.0f);
     }
 
-    __device__ __forceinline__ int operator()(uint32_t r, uint32_t g, uint32_t b, float &o0, float &o1,
-                                              float &o2) const
+    __device__ __forceinline__ Sel<METHOD> select(uint32_t r, uint32_t g, uint32_t b) const
     {
-        const int sR = st.r(), sG = st.g(), sB = 1;
-        int base;
+        // node strides, or record slot strides in the caching layout
+        const int sR = CACHED ? 4 : st.r(), sG = CACHED ? 2 : st.g(), sB = 1;
+        Sel<METHOD> q;
         float fr, fg, fb;
         if (kLocateByTable) {
             const AxisEntry er = tab[r], eg = tab[256 + g], eb = tab[512 + b];
-            base = er.off + eg.off + eb.off;
+            q.base = er.off + eg.off + eb.off;
             fr = er.f; fg = eg.f; fb = eb.f;
         } else {
             const int n = st.g();
@@ -146,75 +205,141 @@ struct OpLut {
             locate(r, n, ir, fr);
             locate(g, n, ig, fg);
             locate(b, n, ib, fb);
-            base = ir * sR + ig * sG + ib;
+            q.base = (ir * n + ig) * n + ib;
+            if (CACHED) q.rec = (ir * (n - 1) + ig) * (n - 1) + ib;
         }
-        const float4 *cb = lut + base;
-        auto c = [cb](int k) { return node<SMEM>(cb + k); };
-        float4 v;
-        int simplex;
         if (METHOD == MACT_TRILINEAR) {
-            const float4 c000 = c(0), c001 = c(sB), c010 = c(sG), c011 = c(sG + sB), c100 = c(sR),
-                         c101 = c(sR + sB), c110 = c(sR + sG), c111 = c(sR + sG + sB);
-            // repeated linear interpolation along B, then G, then R
-            const float4 c00 = f4fma(f4sub(c001, c000), fb, c000);
-            const float4 c01 = f4fma(f4sub(c011, c010), fb, c010);
-            const float4 c10 = f4fma(f4sub(c101, c100), fb, c100);
-            const float4 c11 = f4fma(f4sub(c111, c110), fb, c110);
-            const float4 c0 = f4fma(f4sub(c01, c00), fg, c00);
-            const float4 c1 = f4fma(f4sub(c11, c10), fg, c10);
-            v = f4fma(f4sub(c1, c0), fr, c0);
-            simplex = 0;
+            const int o[8] = {0, sB, sG, sG + sB, sR, sR + sB, sR + sG, sR + sG + sB};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) q.off[k] = o[k];
+            q.simplex = 0;
+            q.w0 = fb; q.w1 = fg; q.w2 = fr;
         } else if (METHOD == MACT_PRISM) {
             // prism axis R; triangle in the G-B face chosen by rem_G >= rem_B
             const bool lo = fg >= fb;
             const int oe = lo ? sG : sB;   // c010 or c001
-            const float4 c000 = c(0), c100 = c(sR), c011 = c(sG + sB), c111 = c(sR + sG + sB);
-            const float4 ce0 = c(oe), ce1 = c(sR + oe);
-            const float fa = lo ? fg : fb, fc = lo ? fb : fg;
-            const float4 t0 = f4fma(f4sub(c011, ce0), fc, f4fma(f4sub(ce0, c000), fa, c000));
-            const float4 t1 = f4fma(f4sub(c111, ce1), fc, f4fma(f4sub(ce1, c100), fa, c100));
-            v = f4fma(f4sub(t1, t0), fr, t0);
-            simplex = lo ? 0 : 1;
+            const int o[6] = {0, sR, sG + sB, sR + sG + sB, oe, sR + oe};
+#pragma unroll
+            for (int k = 0; k < 6; ++k) q.off[k] = o[k];
+            q.simplex = lo ? 0 : 1;
+            q.w0 = lo ? fg : fb; q.w1 = lo ? fb : fg; q.w2 = fr;
         } else if (METHOD == MACT_PYRAMID) {
             // apex c111; base on the face of the smallest fraction (B, then G, then R)
             int oX, oY;
-            float fX, fY, fZ;
-            if (fb <= fr && fb <= fg) { oX = sR; oY = sG; fX = fr; fY = fg; fZ = fb; simplex = 0; }
-            else if (fg <= fr && fg <= fb) { oX = sR; oY = sB; fX = fr; fY = fb; fZ = fg; simplex = 1; }
-            else { oX = sG; oY = sB; fX = fg; fY = fb; fZ = fr; simplex = 2; }
-            const float4 c000 = c(0), c111 = c(sR + sG + sB);
-            const float4 cX = c(oX), cY = c(oY), cA = c(oX + oY);
-            // c000 + (c111-cA) fZ + (cX-c000) fX + (cY-c000) fY + (cA-cX-cY+c000) fX fY
-            const float4 cross = f4add(f4sub(f4sub(cA, cX), cY), c000);
-            float4 acc = f4fma(f4sub(c111, cA), fZ, c000);
-            acc = f4fma(f4sub(cX, c000), fX, acc);
-            acc = f4fma(f4sub(cY, c000), fY, acc);
-            v = f4fma(cross, fX * fY, acc);
+            if (fb <= fr && fb <= fg) { oX = sR; oY = sG; q.w0 = fr; q.w1 = fg; q.w2 = fb; q.simplex = 0; }
+            else if (fg <= fr && fg <= fb) { oX = sR; oY = sB; q.w0 = fr; q.w1 = fb; q.w2 = fg; q.simplex = 1; }
+            else { oX = sG; oY = sB; q.w0 = fg; q.w1 = fb; q.w2 = fr; q.simplex = 2; }
+            const int o[5] = {0, sR + sG + sB, oX, oY, oX + oY};
+#pragma unroll
+            for (int k = 0; k < 5; ++k) q.off[k] = o[k];
         } else {
             // tetrahedral: path from c000 along the axes in decreasing fraction
             int o1, o2;
-            float f1, f2, f3;
-            if (fr >= fg && fg >= fb)      { o1 = sR; o2 = sR + sG; f1 = fr; f2 = fg; f3 = fb; simplex = 0; }
-            else if (fr >= fb && fb > fg)  { o1 = sR; o2 = sR + sB; f1 = fr; f2 = fb; f3 = fg; simplex = 1; }
-            else if (fb > fr && fr >= fg)  { o1 = sB; o2 = sR + sB; f1 = fb; f2 = fr; f3 = fg; simplex = 2; }
-            else if (fg > fr && fr >= fb)  { o1 = sG; o2 = sR + sG; f1 = fg; f2 = fr; f3 = fb; simplex = 3; }
-            else if (fg >= fb && fb > fr)  { o1 = sG; o2 = sG + sB; f1 = fg; f2 = fb; f3 = fr; simplex = 4; }
-            else                           { o1 = sB; o2 = sG + sB; f1 = fb; f2 = fg; f3 = fr; simplex = 5; }
-            const float4 c000 = c(0), c1 = c(o1), c2 = c(o2), c111 = c(sR + sG + sB);
-            float4 acc = f4fma(f4sub(c1, c000), f1, c000);
-            acc = f4fma(f4sub(c2, c1), f2, acc);
-            v = f4fma(f4sub(c111, c2), f3, acc);
+            if (fr >= fg && fg >= fb)      { o1 = sR; o2 = sR + sG; q.w0 = fr; q.w1 = fg; q.w2 = fb; q.simplex = 0; }
+            else if (fr >= fb && fb > fg)  { o1 = sR; o2 = sR + sB; q.w0 = fr; q.w1 = fb; q.w2 = fg; q.simplex = 1; }
+            else if (fb > fr && fr >= fg)  { o1 = sB; o2 = sR + sB; q.w0 = fb; q.w1 = fr; q.w2 = fg; q.simplex = 2; }
+            else if (fg > fr && fr >= fb)  { o1 = sG; o2 = sR + sG; q.w0 = fg; q.w1 = fr; q.w2 = fb; q.simplex = 3; }
+            else if (fg >= fb && fb > fr)  { o1 = sG; o2 = sG + sB; q.w0 = fg; q.w1 = fb; q.w2 = fr; q.simplex = 4; }
+            else                           { o1 = sB; o2 = sG + sB; q.w0 = fb; q.w1 = fg; q.w2 = fr; q.simplex = 5; }
+            const int o[4] = {0, o1, o2, sR + sG + sB};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q.off[k] = o[k];
         }
+        return q;
+    }
+
+    __device__ __forceinline__ void load(const Sel<METHOD> &q, float4 (&nd)[K]) const
+    {
+        const float4 *cb = CACHED ? lut + (int64_t)q.rec * 8 : lut + q.base;
+#pragma unroll
+        for (int k = 0; k < K; ++k) nd[k] = node<SMEM>(cb + q.off[k]);
+    }
+
+    // value from the loaded nodes: directly, or c000 + interpolated differences
+    __device__ __forceinline__ static float4 value(const float4 (&nd)[K], const Sel<METHOD> &q)
+    {
+        if (!CACHED) return interp(nd, q);
+        float4 d[K];
+        d[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 1; k < K; ++k) d[k] = nd[k];
+        return f4add(nd[0], interp(d, q));
+    }
+
+    __device__ __forceinline__ static float4 interp(const float4 (&nd)[K], const Sel<METHOD> &q)
+    {
+        if (METHOD == MACT_TRILINEAR) {
+            // repeated linear interpolation along B, then G, then R
+            // nd: c000 c001 c010 c011 c100 c101 c110 c111
+            const float4 c00 = f4fma(f4sub(nd[1], nd[0]), q.w0, nd[0]);
+            const float4 c01 = f4fma(f4sub(nd[3], nd[2]), q.w0, nd[2]);
+            const float4 c10 = f4fma(f4sub(nd[5], nd[4]), q.w0, nd[4]);
+            const float4 c11 = f4fma(f4sub(nd[7], nd[6]), q.w0, nd[6]);
+            const float4 c0 = f4fma(f4sub(c01, c00), q.w1, c00);
+            const float4 c1 = f4fma(f4sub(c11, c10), q.w1, c10);
+            return f4fma(f4sub(c1, c0), q.w2, c0);
+        } else if (METHOD == MACT_PRISM) {
+            // nd: c000 c100 c011 c111 ce0 ce1; triangle at R = 0 and R = 1, then linear in R
+            const float4 t0 = f4fma(f4sub(nd[2], nd[4]), q.w1, f4fma(f4sub(nd[4], nd[0]), q.w0, nd[0]));
+            const float4 t1 = f4fma(f4sub(nd[3], nd[5]), q.w1, f4fma(f4sub(nd[5], nd[1]), q.w0, nd[1]));
+            return f4fma(f4sub(t1, t0), q.w2, t0);
+        } else if (METHOD == MACT_PYRAMID) {
+            // nd: c000 c111 cX cY cA;
+            // c000 + (c111-cA) fZ + (cX-c000) fX + (cY-c000) fY + (cA-cX-cY+c000) fX fY
+            const float4 cross = f4add(f4sub(f4sub(nd[4], nd[2]), nd[3]), nd[0]);
+            float4 acc = f4fma(f4sub(nd[1], nd[4]), q.w2, nd[0]);
+            acc = f4fma(f4sub(nd[2], nd[0]), q.w0, acc);
+            acc = f4fma(f4sub(nd[3], nd[0]), q.w1, acc);
+            return f4fma(cross, q.w0 * q.w1, acc);
+        } else {
+            // nd: c000 c1 c2 c111
+            float4 acc = f4fma(f4sub(nd[1], nd[0]), q.w0, nd[0]);
+            acc = f4fma(f4sub(nd[2], nd[1]), q.w1, acc);
+            return f4fma(f4sub(nd[3], nd[2]), q.w2, acc);
+        }
+    }
+
+    __device__ __forceinline__ int operator()(uint32_t r, uint32_t g, uint32_t b, float &o0, float &o1,
+                                              float &o2) const
+    {
+        const Sel<METHOD> q = select(r, g, b);
+        float4 nd[K];
+        load(q, nd);
+        const float4 v = value(nd, q);
         o0 = v.x;
         o1 = v.y;
         o2 = v.z;
-        return base * 8 + simplex;
+        return q.base * 8 + q.simplex;
+    }
+
+    // The thread's 4 consecutive pixels: nodes are read again only when the
+    // cell or the simplex changes from the previous pixel (neighbouring
+    // pixels of natural and synthetic images usually share both).
+    __device__ __forceinline__ void quad(const uint32_t (&r)[4], const uint32_t (&g)[4], const uint32_t (&b)[4],
+                                         float (&v)[3][4], int (&sl)[4]) const
+    {
+        float4 nd[K];
+        int prev = -1;
+#pragma unroll 1
+        for (int j = 0; j < 4; ++j) {
+            const Sel<METHOD> q = select(r[j], g[j], b[j]);
+            const int key = q.base * 8 + q.simplex;
+            if (key != prev) {
+                load(q, nd);
+                prev = key;
+            }
+            const float4 o = value(nd, q);
+            v[0][j] = o.x;
+            v[1][j] = o.y;
+            v[2][j] = o.z;
+            sl[j] = key;
+        }
     }
 };
 
 // SMEM: stage the packed float3 LUT as float4 nodes in shared memory.
 // Otherwise lut4 is the float4 copy in global memory.
-template <int THREADS, int MINB, int METHOD, int N, bool SMEM, bool SEL>
+template <int THREADS, int MINB, int METHOD, int N, bool SMEM, bool SEL, bool CACHED = false>
 __global__ void __launch_bounds__(THREADS, MINB)
 k_lut_interp(const __grid_constant__ ImageDesc im, const float *__restrict__ lut, const float4 *__restrict__ lut4,
              int n, int32_t *sel, int64_t ntiles)
@@ -223,7 +348,7 @@ k_lut_interp(const __grid_constant__ ImageDesc im, const float *__restrict__ lut
     __shared__ uint4 sbuf[TileShape<THREADS>::vecs];
     __shared__ AxisEntry stab[kLocateByTable ? 3 * 256 : 1];
     if (kLocateByTable) fill_axis_tables(stab, n);
-    OpLut<METHOD, N, SMEM> op;
+    OpLut<METHOD, N, SMEM, CACHED> op;
     if constexpr (SMEM) {
         const int nodes = n * n * n;
         for (int i = threadIdx.x; i < nodes; i += THREADS)
@@ -237,13 +362,13 @@ k_lut_interp(const __grid_constant__ ImageDesc im, const float *__restrict__ lut
     run_image<THREADS, float, SEL>(im, ntiles, op, sbuf, sel);
 }
 
-template <int THREADS, int MINB, int METHOD, int N, bool SMEM, bool SEL>
+template <int THREADS, int MINB, int METHOD, int N, bool SMEM, bool SEL, bool CACHED = false>
 static cudaError_t launch_interp(const mact_ctx &h, const ImageDesc &im, const float *lut, const float4 *lut4,
                                  int n, int32_t *sel, cudaStream_t s)
 {
     const int64_t nt = tiles_of_t<THREADS>(im);
     if (nt == 0) return cudaSuccess;
-    auto kern = k_lut_interp<THREADS, MINB, METHOD, N, SMEM, SEL>;
+    auto kern = k_lut_interp<THREADS, MINB, METHOD, N, SMEM, SEL, CACHED>;
     const size_t smem = SMEM ? (size_t)n * n * n * sizeof(float4) : 0;
     static int occ_cache[kLutSmemMaxN + 1] = {0};
     int &occ = occ_cache[SMEM ? n : 0];
@@ -304,6 +429,46 @@ cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut,
     case MACT_PRISM: return interp_method<MACT_PRISM>(h, im, d_lut, d_lut4, n, d_sel, s);
     case MACT_PYRAMID: return interp_method<MACT_PYRAMID>(h, im, d_lut, d_lut4, n, d_sel, s);
     default: return interp_method<MACT_TETRA>(h, im, d_lut, d_lut4, n, d_sel, s);
+    }
+}
+
+template <int METHOD, int N>
+static cudaError_t cached_sel(const mact_ctx &h, const ImageDesc &im, const float4 *cache, int n, int32_t *sel,
+                              cudaStream_t s)
+{
+    if (sel) return launch_interp<kThreads, 4, METHOD, N, false, true, true>(h, im, nullptr, cache, n, sel, s);
+    return launch_interp<kThreads, 4, METHOD, N, false, false, true>(h, im, nullptr, cache, n, sel, s);
+}
+
+template <int METHOD>
+static cudaError_t cached_method(const mact_ctx &h, const ImageDesc &im, const float4 *cache, int n, int32_t *sel,
+                                 cudaStream_t s)
+{
+    if (n == 17) return cached_sel<METHOD, 17>(h, im, cache, n, sel, s);
+    if (n == 33) return cached_sel<METHOD, 33>(h, im, cache, n, sel, s);
+    return cached_sel<METHOD, 0>(h, im, cache, n, sel, s);
+}
+
+cudaError_t launch_lut_interp_cached(const mact_ctx &h, int method, const float4 *d_cache, int n,
+                                     const uint8_t *d_rgb, int64_t npix, float *const out[3], int32_t *d_sel,
+                                     cudaStream_t s)
+{
+    ImageDesc im{};
+    im.rgb = d_rgb;
+    for (int c = 0; c < 3; ++c) im.out[c] = out[c];
+    im.width = npix;
+    im.height = 1;
+    im.pitch = 3 * npix;
+    im.opitch = npix;
+    im.space = MACT_CIELAB;
+    im.dtype = MACT_F32;
+    const int P = TileShape<kThreads>::px;
+    im.tiles_per_row = (npix + P - 1) / P;
+    switch (method) {
+    case MACT_TRILINEAR: return cached_method<MACT_TRILINEAR>(h, im, d_cache, n, d_sel, s);
+    case MACT_PRISM: return cached_method<MACT_PRISM>(h, im, d_cache, n, d_sel, s);
+    case MACT_PYRAMID: return cached_method<MACT_PYRAMID>(h, im, d_cache, n, d_sel, s);
+    default: return cached_method<MACT_TETRA>(h, im, d_cache, n, d_sel, s);
     }
 }
 

@@ -112,6 +112,11 @@ def lib():
                      "mact_batch_plan_destroy", "mact_autotune_batch", "mact_set_batch_shape",
                      "mact_get_batch_shape"):
             getattr(L, name).restype = ctypes.c_int
+        L.mact_lut_cache_build.argtypes = [_VP, _VP, ctypes.c_int32, _VP, _VP]
+        L.mact_lut_interp_cached.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32, _VP, ctypes.c_int64,
+                                             ctypes.POINTER(_VP * 3), _VP, _VP]
+        L.mact_lut_cache_build.restype = ctypes.c_int
+        L.mact_lut_interp_cached.restype = ctypes.c_int
         L.mact_cube_error.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double)]
         L.mact_cube_error_lut.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
@@ -492,6 +497,32 @@ def mact_serve_stats(srv):
 
 def mact_serve_destroy(srv, timeout_ms=60000.0):
     return srv.close(timeout_ms)
+
+
+def mact_lut_cache_build(h, lut, out=None, stream=None):
+    """Caching layout of an (n, n, n, 3) FP32 LUT: ((n-1)^3, 8, 4) float32."""
+    n = lut.shape[0]
+    if out is None:
+        out = torch.empty(((n - 1) ** 3, 8, 4), dtype=torch.float32, device=lut.device)
+    _check(lib().mact_lut_cache_build(h.ptr, _VP(lut.data_ptr()), n, _VP(out.data_ptr()), _stream(stream)),
+           "mact_lut_cache_build")
+    return out
+
+
+def mact_lut_interp_cached(h, method, cache, n, rgb, out=None, sel=False, stream=None):
+    """As mact_lut_interp, from the caching layout of an n^3 LUT."""
+    if rgb.dtype != torch.uint8 or not rgb.is_contiguous() or rgb.shape[-1] != 3:
+        raise ValueError("rgb must be a contiguous (..., 3) uint8 tensor")
+    npix = rgb.numel() // 3
+    if out is None:
+        out = torch.empty((3, npix), dtype=torch.float32, device=rgb.device)
+    ptrs = (_VP * 3)(*(out[c].data_ptr() for c in range(3)))
+    s = torch.empty(npix, dtype=torch.int32, device=rgb.device) if sel else None
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    _check(lib().mact_lut_interp_cached(h.ptr, m, _VP(cache.data_ptr()), n, _VP(rgb.data_ptr()), npix,
+                                        ctypes.byref(ptrs), _VP(s.data_ptr() if s is not None else 0),
+                                        _stream(stream)), "mact_lut_interp_cached")
+    return (out, s) if sel else out
 
 
 def mact_strerror(status):

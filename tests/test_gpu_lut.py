@@ -78,3 +78,47 @@ def test_interp_without_selection_output(h, cube_rgb):
     b, _ = mact.mact_lut_interp(h, "tetra", torch.from_numpy(lut).cuda(), rgb, sel=True)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("N", [9, 17, 33])
+def test_cache_layout_records(h, N):
+    """Caching layout: record of cell (i,j,k) = [c000, c_xyz - c000 ...] in
+    slot order x*4 + y*2 + z, computed in FP32 exactly as numpy does."""
+    lut = oracle_lut(N)
+    cache = mact.mact_lut_cache_build(h, torch.from_numpy(lut).cuda()).cpu().numpy()
+    m = N - 1
+    rec = cache.reshape(m, m, m, 8, 4)
+    assert np.array_equal(rec[..., 0, :3], lut[:m, :m, :m])
+    for slot in range(1, 8):
+        x, y, z = slot >> 2, (slot >> 1) & 1, slot & 1
+        d = lut[x:x + m, y:y + m, z:z + m] - lut[:m, :m, :m]
+        assert np.array_equal(rec[..., slot, :3], d)
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("N", [9, 17, 33])
+def test_cached_interp_full_cube(h, cube_rgb, method, N):
+    """The caching form selects the same cells and simplices (bit-identical
+    ids) and gives the same values within 2e-4."""
+    lut = oracle_lut(N)
+    rgb = cube_rgb.reshape(-1, 3)
+    cache = mact.mact_lut_cache_build(h, torch.from_numpy(lut).cuda())
+    out, sel = mact.mact_lut_interp_cached(h, method, cache, N, torch.from_numpy(rgb).cuda(), sel=True)
+    torch.cuda.synchronize()
+    ref, rsel = O.lut_interp(method, lut, rgb)
+    assert np.array_equal(sel.cpu().numpy(), rsel)
+    for c in range(3):
+        assert np.abs(to_np(out[c]) - ref[c]).max() <= LAB_TOL
+
+
+def test_cached_interp_ragged(h):
+    rng = np.random.default_rng(77)
+    lut = rng.normal(scale=40.0, size=(5, 5, 5, 3)).astype(np.float32)
+    cache = mact.mact_lut_cache_build(h, torch.from_numpy(lut).cuda())
+    for npix in (1, 3, 4097):
+        rgb = rng.integers(0, 256, size=(npix, 3), dtype=np.uint8)
+        out, sel = mact.mact_lut_interp_cached(h, "pyramid", cache, 5, torch.from_numpy(rgb).cuda(), sel=True)
+        ref, rsel = O.lut_interp("pyramid", lut, rgb)
+        assert np.array_equal(sel.cpu().numpy(), rsel)
+        for c in range(3):
+            assert np.abs(to_np(out[c]) - ref[c]).max() <= LAB_TOL
