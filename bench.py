@@ -547,10 +547,10 @@ class PinnedPool:
     def give(self, buf):
         self.free[buf.numel() * 4].append(buf)
 
-    def warm(self, sizes, per_class=6):
+    def warm(self, sizes, per_class=16):
         want = collections.Counter(self.cls(n) for n in sizes)
         for c in sorted(want):
-            for _ in range(min(want[c], per_class if c <= (64 << 20) else 2)):
+            for _ in range(min(want[c], per_class if c <= (64 << 20) else 4)):
                 if self.total + c <= self.cap:
                     self.free[c].append(self._new(c))
 
@@ -582,35 +582,46 @@ def run_serve_workload(args):
         return d
 
     results = {}
-    # served
+    # served: the driver submits at each arrival time and, while waiting for
+    # the next one, retires every finished request (its buffer returns to the
+    # pool)
     h = mact.mact_create()
     srv = mact.mact_serve_create(h, 16 << 30, max_slots=128)
-    inflight = collections.deque()    # (ticket, arrival, submit, buffer)
+    inflight = collections.OrderedDict()    # ticket -> (arrival, submit, buffer)
     lat = []
     npx = 0
 
-    def retire_one():
-        tk, ta, t_sub, buf = inflight.popleft()
-        mact.mact_serve_wait(srv, tk, 600000)
+    def retire(tk, wait=False):
+        ta, t_sub, buf = inflight.pop(tk)
+        if wait:
+            mact.mact_serve_wait(srv, tk, 600000)
         _, server_ms = mact.mact_serve_poll(srv, tk)
         mact.mact_serve_release(srv, tk)
         outs.give(buf)
         lat.append((t_sub - ta) * 1e3 + server_ms)
 
+    def reap():
+        done = [tk for tk in inflight if mact.mact_serve_poll(srv, tk)[0]]
+        for tk in done:
+            retire(tk)
+        return bool(done)
+
+    def reclaim():                             # pool exhausted: wait for the oldest
+        if not reap():
+            retire(next(iter(inflight)), wait=True)
+
     t0 = time.perf_counter()
     for ta, hgt, wid, _, space in trace:
         while time.perf_counter() - t0 < ta:
-            if inflight and mact.mact_serve_poll(srv, inflight[0][0])[0]:
-                retire_one()
-            else:
+            if not (inflight and reap()):
                 time.sleep(5e-5)
-        buf = outs.take(12 * hgt * wid, reclaim=retire_one)
+        buf = outs.take(12 * hgt * wid, reclaim=reclaim)
         t_sub = time.perf_counter() - t0
         tk, _ = mact.mact_serve_submit(srv, req_in(hgt, wid), space, out=buf[: 3 * hgt * wid].view(3, hgt, wid))
-        inflight.append((tk, ta, t_sub, buf))
+        inflight[tk] = (ta, t_sub, buf)
         npx += hgt * wid
     while inflight:
-        retire_one()
+        retire(next(iter(inflight)), wait=True)
     wall = time.perf_counter() - t0
     st = mact.mact_serve_stats(srv)
     srv.close()
