@@ -600,11 +600,22 @@ def run_serve_workload(args):
         outs.give(buf)
         lat.append((t_sub - ta) * 1e3 + server_ms)
 
+    last_scan = [0.0]
+
     def reap():
-        done = [tk for tk in inflight if mact.mact_serve_poll(srv, tk)[0]]
-        for tk in done:
-            retire(tk)
-        return bool(done)
+        """Retire finished requests: from the oldest while they are done (the
+        server is first-in first-out), and every 2 ms a full scan."""
+        n = 0
+        while inflight and mact.mact_serve_poll(srv, next(iter(inflight)))[0]:
+            retire(next(iter(inflight)))
+            n += 1
+        now = time.perf_counter()
+        if now - last_scan[0] > 2e-3:
+            last_scan[0] = now
+            for tk in [tk for tk in inflight if mact.mact_serve_poll(srv, tk)[0]]:
+                retire(tk)
+                n += 1
+        return n > 0
 
     def reclaim():                             # pool exhausted: wait for the oldest
         if not reap():

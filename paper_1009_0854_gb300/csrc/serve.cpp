@@ -187,8 +187,13 @@ static bool serve_tick(mact_server *s)
             if (r->in_host) {
                 r->d_in = base;
                 const size_t sp = H == 1 ? (size_t)(3 * W) : (size_t)im.pitch_bytes;   // one row: pitch unused
-                if (e == cudaSuccess)
-                    e = cudaMemcpy2DAsync(r->d_in, 3 * W, im.rgb, sp, 3 * W, H, cudaMemcpyHostToDevice, s->s_h2d);
+                if (e == cudaSuccess) {
+                    if (sp == (size_t)(3 * W))   // contiguous rows: one linear copy
+                        e = cudaMemcpyAsync(r->d_in, im.rgb, (size_t)(3 * W) * H, cudaMemcpyHostToDevice, s->s_h2d);
+                    else
+                        e = cudaMemcpy2DAsync(r->d_in, 3 * W, im.rgb, sp, 3 * W, H, cudaMemcpyHostToDevice,
+                                              s->s_h2d);
+                }
                 im.rgb = r->d_in;
                 im.pitch_bytes = 3 * W;
             }
@@ -217,9 +222,21 @@ static bool serve_tick(mact_server *s)
             const int64_t W = im.width, H = im.height;
             if (r->out_host) {
                 const size_t dp = H == 1 ? (size_t)W * r->elem : (size_t)im.out_pitch_elems * r->elem;
-                for (int c = 0; c < 3 && e == cudaSuccess; ++c)
-                    e = cudaMemcpy2DAsync(im.out[c], dp, r->d_out[c], W * r->elem, W * r->elem, H,
-                                          cudaMemcpyDeviceToHost, s->s_d2h);
+                const size_t row = (size_t)W * r->elem;
+                const bool planes_adjacent = dp == row &&
+                    static_cast<char *>(im.out[1]) == static_cast<char *>(im.out[0]) + row * H &&
+                    static_cast<char *>(im.out[2]) == static_cast<char *>(im.out[1]) + row * H;
+                if (planes_adjacent) {   // one linear copy of all three planes
+                    e = cudaMemcpyAsync(im.out[0], r->d_out[0], 3 * row * H, cudaMemcpyDeviceToHost, s->s_d2h);
+                } else {
+                    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+                        if (dp == row)
+                            e = cudaMemcpyAsync(im.out[c], r->d_out[c], row * H, cudaMemcpyDeviceToHost, s->s_d2h);
+                        else
+                            e = cudaMemcpy2DAsync(im.out[c], dp, r->d_out[c], row, row, H, cudaMemcpyDeviceToHost,
+                                                  s->s_d2h);
+                    }
+                }
             }
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_done, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventRecord(r->ev_done, s->s_d2h);
