@@ -246,8 +246,10 @@ def run_gpu(args):
                    "hbm_frac": round(PIX * bytes_px / (row_ms[name] * 1e-3) / 1e9 / hbm, 4)}
             for name in row_ms}
 
-    # end to end through the C ABI with host buffers: pinned H2D of the input,
-    # every row, D2H of every output plane, all inside the timed region
+    # end to end through the C ABI with host buffers, inside the timed region:
+    # the pinned input is copied to the device once, and every row's kernel
+    # writes its three planes straight into pinned host memory across the host
+    # link (the kernels address mapped host memory; no staging copy)
     e2e = None
     if not args.no_e2e:
         pin_in = cube_h.pin_memory()
@@ -257,9 +259,7 @@ def run_gpu(args):
         def e2e_step():
             dev_in.copy_(pin_in, non_blocking=True)
             for name, kind, arg in ROWS:
-                run_row(name, kind, arg, dev_in, outs[name])
-            for name, _, _ in ROWS:
-                pin_out[name].copy_(outs[name], non_blocking=True)
+                run_row(name, kind, arg, dev_in, pin_out[name])
 
         for _ in range(2):
             e2e_step()
@@ -503,72 +503,88 @@ def run_lut_workload(args):
     print(json.dumps({"workload": "lut: standard vs caching layout, cube and uniform noise, 2^24 px", "rows": rows}))
 
 
-class PinnedPool:
-    """Pinned host buffers for request outputs, by power-of-two size class,
-    reused last-in-first-out (as a server recycles response buffers), with a
-    cap on the total pinned bytes."""
+class PinnedRing:
+    """Request output buffers carved from one pinned host allocation, made
+    before the run: first in, first out, with out-of-order release (a slot is
+    reused once every older slot is released too).  When the ring is full,
+    take() calls reclaim() (which must release the oldest request) until the
+    new buffer fits: back-pressure instead of a pinned allocation mid-run."""
 
-    def __init__(self, torch, cap_bytes=10 << 30):
-        self.torch = torch
-        self.free = collections.defaultdict(list)
-        self.cap = cap_bytes
-        self.total = 0
+    ALIGN = 256
 
-    @staticmethod
-    def cls(n):
-        return max(1 << 20, 1 << (int(n) - 1).bit_length())
+    def __init__(self, torch, nbytes):
+        self.buf = torch.empty(nbytes // 4, dtype=torch.float32).pin_memory()
+        self.n = (nbytes // 4) * 4
+        self.head = 0
+        self.live = collections.deque()      # [offset, size, released]
 
-    def _new(self, c):
-        self.total += c
-        return self.torch.empty(c // 4, dtype=self.torch.float32).pin_memory()
+    def _fit(self, size):
+        if not self.live:
+            self.head = 0
+            return 0 if size <= self.n else None
+        tail = self.live[0][0]
+        if self.head > tail:                  # occupied [tail, head): free [head, n) and [0, tail)
+            if self.head + size <= self.n:
+                return self.head
+            return 0 if size <= tail else None
+        return self.head if self.head + size <= tail else None   # wrapped: free [head, tail)
 
-    def take(self, n, reclaim=None):
-        """A buffer of at least n bytes; when the cap is reached, reclaim()
-        (which must return one buffer to the pool) is called until one of
-        this class is free or room is made."""
-        c = self.cls(n)
+    def take(self, nbytes, reclaim):
+        size = -(-nbytes // self.ALIGN) * self.ALIGN
+        if size > self.n:
+            raise MemoryError("request larger than the output ring")
         while True:
-            if self.free[c]:
-                return self.free[c].pop()
-            if self.total + c <= self.cap:
-                return self._new(c)
-            freed = False
-            for oc in sorted(self.free):           # drop idle buffers of other classes
-                if oc != c and self.free[oc]:
-                    self.free[oc].pop()
-                    self.total -= oc
-                    freed = True
-                    break
-            if not freed:
-                if reclaim is None:
-                    raise MemoryError("pinned pool exhausted")
-                reclaim()
+            off = self._fit(size)
+            if off is not None:
+                break
+            reclaim()
+        entry = [off, size, False]
+        self.live.append(entry)
+        self.head = off + size
+        return self.buf[off // 4: (off + nbytes) // 4], entry
 
-    def give(self, buf):
-        self.free[buf.numel() * 4].append(buf)
-
-    def warm(self, sizes, per_class=16):
-        want = collections.Counter(self.cls(n) for n in sizes)
-        for c in sorted(want):
-            for _ in range(min(want[c], per_class if c <= (64 << 20) else 4)):
-                if self.total + c <= self.cap:
-                    self.free[c].append(self._new(c))
+    def give(self, entry):
+        entry[2] = True
+        while self.live and self.live[0][2]:
+            self.live.popleft()
 
 
 def run_serve_workload(args):
     """Poisson arrivals (2000/s) of 0.1-24 Mpx images, 50/25/25% CIELAB/HSI/SCT,
-    pinned host input and output (output buffers from a LIFO pool shared by
-    both paths), through the continuous-batching server (MACT, 16 GB staging
-    budget) and through the plain path (one request at a time: H2D,
-    exact-libm kernel, D2H).  Latency counts from the trace's arrival time."""
+    pinned host input and output (outputs carved from one pinned ring shared by
+    every path), through the continuous-batching server (MACT, 16 GB staging
+    budget) in direct mode (the kernel reads and writes the pinned buffers in
+    place) and in staged mode (copies through the arena), and through the
+    plain path (one request at a time: H2D, exact-libm kernel, D2H).  Every
+    path first serves an untimed 0.25 s warm-up trace.  Latency counts from
+    the trace's arrival time."""
     import torch
     from paper_1009_0854_gb300 import mact, synth
     dev = torch.device("cuda", 0)
     trace = synth.serve_trace(rate=2000.0, duration=args.serve_seconds, seed=0)
-    maxpx = max(h * w for _, h, w, _, _ in trace)
+    warm_trace = synth.serve_trace(rate=2000.0, duration=0.25, seed=1)
+    maxpx = max(h * w for _, h, w, _, _ in trace + warm_trace)
     pool_in = torch.from_numpy(synth.request_image(4096, 6144, 2, 7).reshape(-1)).pin_memory()  # 75 MB
-    outs = PinnedPool(torch)
-    outs.warm([12 * h * w for _, h, w, _, _ in trace])
+    ring = PinnedRing(torch, 16 << 30)
+
+    def link_gbs(dst_views, src):
+        """Copy-engine D2H bandwidth into the given pinned views (one copy each)."""
+        st = torch.cuda.current_stream()
+        for v in dst_views[:2]:
+            v.copy_(src[: v.numel()], non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for v in dst_views:
+            v.copy_(src[: v.numel()], non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return round(sum(v.numel() * 4 for v in dst_views) / (e0.elapsed_time(e1) * 1e-3) / 1e9, 1)
+
+    cal_src = torch.empty(64 << 20, dtype=torch.float32, device=dev)      # 256 MB
+    step = ring.buf.numel() // 16
+    ring_gbs = link_gbs([ring.buf[k * step: k * step + (64 << 20)] for k in range(16)], cal_src)
+    ring0_gbs = link_gbs([ring.buf[: 64 << 20]] * 16, cal_src)
 
     def req_in(hgt, wid):
         return pool_in[: hgt * wid * 3].view(hgt, wid, 3)
@@ -581,87 +597,112 @@ def run_serve_workload(args):
         d.update(extra or {})
         return d
 
-    results = {}
-    # served: the driver submits at each arrival time and, while waiting for
-    # the next one, retires every finished request (its buffer returns to the
-    # pool)
     h = mact.mact_create()
-    srv = mact.mact_serve_create(h, 16 << 30, max_slots=128)
-    inflight = collections.OrderedDict()    # ticket -> (arrival, submit, buffer)
-    lat = []
-    npx = 0
 
-    def retire(tk, wait=False):
-        ta, t_sub, buf = inflight.pop(tk)
-        if wait:
-            mact.mact_serve_wait(srv, tk, 600000)
-        _, server_ms = mact.mact_serve_poll(srv, tk)
-        mact.mact_serve_release(srv, tk)
-        outs.give(buf)
-        lat.append((t_sub - ta) * 1e3 + server_ms)
+    def served(tr, mode):
+        """The driver submits at each arrival time and, while waiting for the
+        next one, retires every finished request (its ring slot is released)."""
+        srv = mact.mact_serve_create(h, 16 << 30, max_slots=128)
+        mact.mact_serve_set_mode(srv, mode)
+        inflight = collections.OrderedDict()    # ticket -> (arrival, submit, ring entry)
+        lat = []
+        stats = {"reclaim_waits": 0, "inflight_max": 0, "lag_max_ms": 0.0}
+        lag_series = []                          # worst lag in each 0.5 s of the trace
 
-    last_scan = [0.0]
+        def retire(tk, wait=False):
+            ta, t_sub, entry = inflight.pop(tk)
+            if wait:
+                mact.mact_serve_wait(srv, tk, 600000)
+            _, server_ms = mact.mact_serve_poll(srv, tk)
+            mact.mact_serve_release(srv, tk)
+            ring.give(entry)
+            lat.append((t_sub - ta) * 1e3 + server_ms)
 
-    def reap():
-        """Retire finished requests: from the oldest while they are done (the
-        server is first-in first-out), and every 2 ms a full scan."""
-        n = 0
-        while inflight and mact.mact_serve_poll(srv, next(iter(inflight)))[0]:
-            retire(next(iter(inflight)))
-            n += 1
-        now = time.perf_counter()
-        if now - last_scan[0] > 2e-3:
-            last_scan[0] = now
-            for tk in [tk for tk in inflight if mact.mact_serve_poll(srv, tk)[0]]:
-                retire(tk)
+        last_scan = [0.0]
+
+        def reap():
+            """Retire finished requests: from the oldest while they are done
+            (the server is first-in first-out), and every 2 ms a full scan."""
+            n = 0
+            while inflight and mact.mact_serve_poll(srv, next(iter(inflight)))[0]:
+                retire(next(iter(inflight)))
                 n += 1
-        return n > 0
+            now = time.perf_counter()
+            if now - last_scan[0] > 2e-3:
+                last_scan[0] = now
+                for tk in [tk for tk in inflight if mact.mact_serve_poll(srv, tk)[0]]:
+                    retire(tk)
+                    n += 1
+            return n > 0
 
-    def reclaim():                             # pool exhausted: wait for the oldest
-        if not reap():
+        def reclaim():                             # ring full: wait for the oldest
+            stats["reclaim_waits"] += 1
+            if not reap():
+                retire(next(iter(inflight)), wait=True)
+
+        npx = 0
+        t0 = time.perf_counter()
+        for ta, hgt, wid, _, space in tr:
+            while time.perf_counter() - t0 < ta:
+                if not (inflight and reap()):
+                    time.sleep(5e-5)
+            buf, entry = ring.take(12 * hgt * wid, reclaim)
+            t_sub = time.perf_counter() - t0
+            tk, _ = mact.mact_serve_submit(srv, req_in(hgt, wid), space, out=buf.view(3, hgt, wid))
+            inflight[tk] = (ta, t_sub, entry)
+            stats["inflight_max"] = max(stats["inflight_max"], len(inflight))
+            stats["lag_max_ms"] = max(stats["lag_max_ms"], round((t_sub - ta) * 1e3, 3))
+            k = int(ta / 0.5)
+            while len(lag_series) <= k:
+                lag_series.append(0.0)
+            lag_series[k] = max(lag_series[k], round((t_sub - ta) * 1e3, 1))
+            npx += hgt * wid
+        while inflight:
             retire(next(iter(inflight)), wait=True)
+        wall = time.perf_counter() - t0
+        st = mact.mact_serve_stats(srv)
+        srv.close()
+        stats["lag_ms_per_half_second"] = lag_series
+        stages = {k[:-3]: round(st[k], 3) for k in ("queue_p50_ms", "h2d_p50_ms", "compute_p50_ms", "d2h_p50_ms",
+                                                   "queue_p99_ms", "h2d_p99_ms", "compute_p99_ms", "d2h_p99_ms")}
+        stages["d2h_busy_ms"] = round(st["d2h_busy_ms"], 1)
+        stages["d2h_copy_gbs"] = round(st["d2h_copy_gbs"], 1)
+        return summary(lat, npx, wall, {"batches": st["batches"], "server_p50_ms": round(st["p50_ms"], 3),
+                                        "server_p99_ms": round(st["p99_ms"], 3), "server_stages_ms": stages,
+                                        "client": stats})
 
-    t0 = time.perf_counter()
-    for ta, hgt, wid, _, space in trace:
-        while time.perf_counter() - t0 < ta:
-            if not (inflight and reap()):
-                time.sleep(5e-5)
-        buf = outs.take(12 * hgt * wid, reclaim=reclaim)
-        t_sub = time.perf_counter() - t0
-        tk, _ = mact.mact_serve_submit(srv, req_in(hgt, wid), space, out=buf[: 3 * hgt * wid].view(3, hgt, wid))
-        inflight[tk] = (ta, t_sub, buf)
-        npx += hgt * wid
-    while inflight:
-        retire(next(iter(inflight)), wait=True)
-    wall = time.perf_counter() - t0
-    st = mact.mact_serve_stats(srv)
-    srv.close()
-    results["served"] = summary(lat, npx, wall, {"batches": st["batches"], "server_p50_ms": round(st["p50_ms"], 3),
-                                                 "server_p99_ms": round(st["p99_ms"], 3)})
     # plain: one request at a time, exact libm kernels
     he = mact.mact_create(exact=1)
     dbuf_in = torch.empty(3 * maxpx, dtype=torch.uint8, device=dev)
     dbuf_out = torch.empty(3 * maxpx, dtype=torch.float32, device=dev)
     s = torch.cuda.current_stream()
-    lat = []
-    npx = 0
-    t0 = time.perf_counter()
-    for ta, hgt, wid, _, space in trace:
-        while time.perf_counter() - t0 < ta:
-            pass
-        inp = req_in(hgt, wid)
-        buf = outs.take(12 * hgt * wid)
-        din = dbuf_in[: hgt * wid * 3].view(hgt, wid, 3)
-        dout = dbuf_out[: 3 * hgt * wid].view(3, hgt, wid)
-        din.copy_(inp, non_blocking=True)
-        mact.mact_convert(he, din, space, out=dout, stream=s)
-        buf[: 3 * hgt * wid].view(3, hgt, wid).copy_(dout, non_blocking=True)
-        s.synchronize()
-        outs.give(buf)
-        lat.append((time.perf_counter() - t0 - ta) * 1e3)
-        npx += hgt * wid
-    wall = time.perf_counter() - t0
-    results["plain_exact_per_image"] = summary(lat, npx, wall)
+
+    def plain(tr):
+        lat = []
+        npx = 0
+        t0 = time.perf_counter()
+        for ta, hgt, wid, _, space in tr:
+            while time.perf_counter() - t0 < ta:
+                pass
+            inp = req_in(hgt, wid)
+            buf, entry = ring.take(12 * hgt * wid, None)     # the ring is empty here: never reclaims
+            din = dbuf_in[: hgt * wid * 3].view(hgt, wid, 3)
+            dout = dbuf_out[: 3 * hgt * wid].view(3, hgt, wid)
+            din.copy_(inp, non_blocking=True)
+            mact.mact_convert(he, din, space, out=dout, stream=s)
+            buf.view(3, hgt, wid).copy_(dout, non_blocking=True)
+            s.synchronize()
+            ring.give(entry)
+            lat.append((time.perf_counter() - t0 - ta) * 1e3)
+            npx += hgt * wid
+        return summary(lat, npx, time.perf_counter() - t0)
+
+    served(warm_trace, "direct")
+    served(warm_trace, "staged")
+    plain(warm_trace)
+    results = {"served_direct": served(trace, "direct"), "served_staged": served(trace, "staged"),
+               "plain_exact_per_image": plain(trace),
+               "link": {"d2h_gbs_ring_spread": ring_gbs, "d2h_gbs_ring_start": ring0_gbs}}
     print(json.dumps({"workload": "serve: Poisson 2000 req/s for %g s, 0.1-24 Mpx, pinned host buffers"
                       % args.serve_seconds, "rows": results}))
 

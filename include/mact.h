@@ -15,10 +15,18 @@
  * Table Interpolation Methods").
  *
  * Conventions for every entry point:
- *  - Pointers named d_* and the pointers inside mact_image are DEVICE
- *    pointers on the current CUDA device, except where a function says host.
- *    The caller owns every image, LUT and output buffer; the library never
- *    frees them.
+ *  - Pointers named d_* and the pointers inside mact_image are pointers the
+ *    kernels dereference: device memory of the current CUDA device, or host
+ *    memory mapped into its address space (cudaHostAlloc, cudaHostRegister;
+ *    and, where mact_host_memory_access returns 1, any host memory).  On host
+ *    memory the kernels read and write across the host link themselves, with
+ *    no staging copy, so their speed is the link's (about 190 GB/s
+ *    device-to-host on a Grace-hosted GB300) rather than HBM's.  Where the
+ *    device cannot address pageable memory, every such pointer is checked
+ *    before launch and unregistered host memory is rejected with
+ *    MACT_E_INVAL.  Functions that take a pointer written by the host (an
+ *    eps_avg, a ticket) say so.  The caller owns every image, LUT and output
+ *    buffer; the library never frees them.
  *  - A handle owns a small device block (gamma table, coefficients) created on
  *    the device that is current when mact_create is called; use the handle on
  *    that device only.
@@ -102,9 +110,9 @@ typedef struct {
     int32_t sct_n, sct_m, sct_r;
 } mact_config;
 
-/* One image.  rgb: device pointer to height rows of width interleaved
- * pixels, rows pitch_bytes apart (>= 3*width).  out[c]: device pointers to
- * the three output planes, rows out_pitch_elems elements apart (>= width),
+/* One image.  rgb: pointer (device, or host memory the device addresses) to
+ * height rows of width interleaved pixels, rows pitch_bytes apart
+ * (>= 3*width).  out[c]: pointers of the same kind to the three output planes, rows out_pitch_elems elements apart (>= width),
  * element type given by dtype.  space: mact_space; dtype: mact_dtype.
  * Fastest when rgb is 16-byte aligned, pitch_bytes == 3*width,
  * out_pitch_elems == width and every out[c] is 16-byte aligned; any other
@@ -141,12 +149,16 @@ mact_status mact_convert(mact_handle h, const mact_image *img, mact_stream strea
 /* Convert count images of any sizes, spaces and dtypes in ONE launch of a
  * persistent kernel that walks a tile work list (the batched form; Section
  * "Calculation of the Computational Gain Values" runs the transforms over an
- * image set).  Each CTA claims 4096-pixel tiles (or the autotuned shape, see
- * mact_autotune_batch) with an atomic counter.  The work
- * list is uploaded from pinned staging into one of 4 device slots owned by
- * the handle (grown on demand), so up to 4 consecutive calls pipeline; a
- * slot is reused only after its previous call's copy and kernel are done.
- * Result of each image equals mact_convert of that image. */
+ * image set).  Tiles are 4096 pixels (or the autotuned shape, see
+ * mact_autotune_batch).  With at most 32 non-empty images the work list is
+ * passed by value in the kernel's parameters: the call makes no copy, takes
+ * no device memory and never waits on the host, and CTAs take tiles
+ * grid-stride.  Longer lists are uploaded from pinned staging into one of 4
+ * device slots owned by the handle (grown on demand), and CTAs claim tiles
+ * with an atomic counter; up to 4 consecutive calls pipeline, and a slot is
+ * reused only after its previous call's copy and kernel are done (the call
+ * may wait on the host for that).  Result of each image equals mact_convert
+ * of that image. */
 mact_status mact_convert_batch(mact_handle h, const mact_image *imgs, int32_t count,
                                mact_stream stream);
 
@@ -271,7 +283,15 @@ mact_status mact_lab_delta_e_loss(mact_handle h, const float *d_x, const float *
  * kernel (as mact_convert_batch), and copies results back, on three streams
  * (H2D, compute, D2H) so the copies of one tick overlap the kernel of
  * another.  Requests that arrive while others are on the GPU join the next
- * tick.  The result of each request equals mact_convert of that image. */
+ * tick.  The result of each request equals mact_convert of that image.
+ *
+ * Host buffers: in direct mode (the default) the kernel reads and writes host
+ * buffers it can address (pinned memory, and any host memory where
+ * mact_host_memory_access returns 1) in place, across the host link, with no
+ * staging and no copy; other host buffers are staged.  In staged mode every
+ * host buffer is staged: input copied into the arena, output copied back. */
+
+enum { MACT_SERVE_DIRECT = 0, MACT_SERVE_STAGED = 1 };
 
 typedef struct {
     int64_t completed;   /* requests finished successfully */
@@ -282,18 +302,36 @@ typedef struct {
     int64_t pixels;      /* pixels of the completed requests */
     double p50_ms, p99_ms, max_ms;  /* submit-to-completion latency of completed requests */
     double gpix_per_s;   /* completed pixels / (last completion - first submit) */
+    /* Stages of that latency, median and 99th percentile over the completed
+     * requests: queue = submit to admission (host clock); h2d = the batch's
+     * input copies; compute = from the end of those copies to the end of the
+     * batch's kernel (waits for the compute stream included); d2h = from the
+     * end of the kernel to the end of the request's output copy (waits behind
+     * earlier output copies included).  The device stages are CUDA-event
+     * times. */
+    double queue_p50_ms, h2d_p50_ms, compute_p50_ms, d2h_p50_ms;
+    double queue_p99_ms, h2d_p99_ms, compute_p99_ms, d2h_p99_ms;
+    /* Output copies to host memory: summed copy time (from the moment the
+     * D2H stream reaches a request's copies to their end) and the bandwidth
+     * they ran at (bytes / that time). */
+    double d2h_busy_ms, d2h_copy_gbs;
 } mact_serve_stats_t;
 
-/* Create a server for handle h (on h's device).  max_slots bounds the number
- * of admitted, unfinished requests (1..65536); mem_budget_bytes (>= 4096)
- * bounds their staging memory.  Device-resident inputs and outputs take no
- * budget. */
+/* Create a server for handle h (on h's device), in direct mode.  max_slots
+ * bounds the number of admitted, unfinished requests (1..65536);
+ * mem_budget_bytes (>= 4096) bounds their staging memory.  Device-resident
+ * inputs and outputs, and host buffers used in place, take no budget. */
 mact_status mact_serve_create(mact_handle h, size_t mem_budget_bytes, int32_t max_slots, mact_server_t *out);
 
+/* How host buffers of requests submitted from now on are used:
+ * MACT_SERVE_DIRECT or MACT_SERVE_STAGED (see above).  MACT_E_INVAL for
+ * another value. */
+mact_status mact_serve_set_mode(mact_server_t srv, int32_t mode);
+
 /* Queue one image.  img->rgb and img->out[] may each be host memory (pinned
- * is fastest; pageable works but its copies block the scheduler) or device
- * memory; host images are staged through the arena.  The buffers must stay
- * valid until the request is done.  Returns a ticket.  MACT_E_NOMEM if the
+ * is fastest; staged pageable memory works but its copies block the
+ * scheduler) or device memory.  The buffers must stay valid until the
+ * request is done.  Returns a ticket.  MACT_E_NOMEM if the
  * request alone needs more staging than the whole budget; MACT_E_BUSY once
  * the server is shutting down. */
 mact_status mact_serve_submit(mact_server_t srv, const mact_image *img, uint64_t *ticket);
@@ -356,6 +394,17 @@ mact_status mact_lut_cache_build(mact_handle h, const float *d_lut, int32_t n, f
 mact_status mact_lut_interp_cached(mact_handle h, int32_t method, const float *d_cache, int32_t n,
                                    const uint8_t *d_rgb, int64_t npix, float *const d_out[3], int32_t *d_sel,
                                    mact_stream stream);
+
+/* Which host memory the kernels of handle h may be given (the paper has no
+ * counterpart: it concerns where the pixels live, not how they are
+ * converted).  Returns 1 when the device addresses any host memory through
+ * the host page tables (cudaDevAttrPageableMemoryAccess, e.g. a Grace-hosted
+ * GB300): pointers are then not checked.  Returns 0 when only device memory
+ * and pinned or registered host memory may be given: every pointer argument
+ * is then checked with cudaPointerGetAttributes before launch.  Setting the
+ * environment variable MACT_CHECK_HOST_POINTERS to a value other than "0"
+ * before mact_create forces 0.  MACT_E_INVAL for a NULL handle. */
+int32_t mact_host_memory_access(mact_handle h);
 
 /* Message for a status code (static storage). */
 const char *mact_strerror(mact_status st);

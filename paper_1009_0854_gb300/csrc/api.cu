@@ -1,6 +1,7 @@
 // api.cu -- the exported C ABI of libmact.so (include/mact.h): argument
 // validation, handle state, work lists, and dispatch to the kernels.
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -184,9 +185,43 @@ mact_status check_image(const mact_image *img)
     if (img->width > (int64_t(1) << 42) || img->height > ((int64_t(1) << 42) / img->width))
         return inval("image too large (more than 2^42 pixels)");
     if (!img->rgb || !img->out[0] || !img->out[1] || !img->out[2]) return inval("NULL image pointer");
+    const uintptr_t esz = img->dtype == MACT_F16 ? 2 : 4;   // the kernels store whole elements
+    for (int c = 0; c < 3; ++c)
+        if (reinterpret_cast<uintptr_t>(img->out[c]) % esz != 0) return inval("out[c] not aligned to its element size");
     if (img->height > 1 && img->pitch_bytes < 3 * img->width) return inval("pitch_bytes < 3*width");
     if (img->height > 1 && img->out_pitch_elems < img->width) return inval("out_pitch_elems < width");
     return MACT_OK;
+}
+
+// Typed arrays the kernels read or write element by element must be aligned
+// to their element size (4 bytes: float, int32).
+static bool aligned4(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
+
+mact_status check_access(const mact_ctx &h, const void *p, const char *what)
+{
+    if (h.any_host || !p) return MACT_OK;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // an unknown pointer leaves an error behind: clear it
+        a.type = cudaMemoryTypeUnregistered;
+    }
+    if (a.type == cudaMemoryTypeUnregistered) {
+        set_error(std::string(what) + ": host memory the device cannot address (pin or register it)");
+        return MACT_E_INVAL;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer != p) {
+        set_error(std::string(what) + ": registered host memory with a different device address");
+        return MACT_E_INVAL;
+    }
+    return MACT_OK;
+}
+
+mact_status check_image_access(const mact_ctx &h, const mact_image &img)
+{
+    if (h.any_host || img.width == 0 || img.height == 0) return MACT_OK;
+    mact_status st = check_access(h, img.rgb, "image rgb");
+    for (int c = 0; c < 3 && st == MACT_OK; ++c) st = check_access(h, img.out[c], "image out");
+    return st;
 }
 
 ImageDesc make_desc(const mact_image &img, int64_t tile_px)
@@ -250,6 +285,9 @@ mact_status mact_create(const mact_config *cfg, mact_handle *out)
     if (st != MACT_OK) { delete h; return st; }
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->any_host, cudaDevAttrPageableMemoryAccess, h->device);
+    if (const char *force = std::getenv("MACT_CHECK_HOST_POINTERS"))
+        if (force[0] != '\0' && force[0] != '0') h->any_host = 0;
     if (e == cudaSuccess) e = cudaMalloc(&h->d_gamma, 256 * (sizeof(float) + sizeof(double)));
     if (e == cudaSuccess) {
         struct { float g32[256]; double g64[256]; } tab;
@@ -296,6 +334,8 @@ mact_status mact_convert(mact_handle h, const mact_image *img, mact_stream strea
     mact_status st = check_image(img);
     if (st != MACT_OK) return st;
     if (img->width == 0 || img->height == 0) return MACT_OK;
+    st = check_image_access(*h, *img);
+    if (st != MACT_OK) return st;
     ImageDesc d = make_desc(*img);
     return cuda_status(launch_convert(*h, d, (cudaStream_t)stream), "mact_convert launch");
 }
@@ -307,9 +347,35 @@ mact_status mact_convert_batch(mact_handle h, const mact_image *imgs, int32_t co
     if (count > 0 && !imgs) return inval("imgs is NULL");
     for (int32_t i = 0; i < count; ++i) {
         mact_status st = check_image(&imgs[i]);
+        if (st == MACT_OK) st = check_image_access(*h, imgs[i]);
         if (st != MACT_OK) return st;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    int32_t nonempty = 0;
+    for (int32_t i = 0; i < count; ++i) nonempty += (imgs[i].width != 0 && imgs[i].height != 0);
+    if (nonempty == 0) return MACT_OK;
+    if (nonempty <= kParamImages) {   // short list: by value in the kernel parameters
+        BatchCfg cfg;
+        {
+            std::lock_guard<std::mutex> lock(h->batch_mu);
+            cfg = h->batch_cfg;
+        }
+        ParamList list{};
+        int64_t total = 0;
+        int32_t n = 0;
+        for (int32_t i = 0; i < count; ++i) {
+            if (imgs[i].width == 0 || imgs[i].height == 0) continue;
+            ImageDesc d = make_desc(imgs[i], cfg.tile_px());
+            d.tile_begin = total;
+            total += tiles_of(d);
+            list.img[n++] = d;
+        }
+        int per_sm = batch_blocks_per_sm(*h, cfg);
+        if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
+        int64_t grid = (int64_t)h->num_sms * per_sm;
+        if (grid > total) grid = total;
+        return cuda_status(launch_batch_param(*h, list, n, total, (int)grid, s, cfg), "mact_convert_batch launch");
+    }
     std::lock_guard<std::mutex> lock(h->batch_mu);
     mact_ctx::BatchSlot &sl = h->batch_slots[h->batch_next];
     h->batch_next = (h->batch_next + 1) % mact_ctx::kBatchSlots;
@@ -363,6 +429,9 @@ mact_status mact_lut_build(mact_handle h, int32_t n, float *d_lut, mact_stream s
     if (!h) return inval("mact_lut_build: NULL handle");
     if (n < 2 || n > 64) return inval("LUT size must be 2..64");
     if (!d_lut) return inval("d_lut is NULL");
+    if (!aligned4(d_lut)) return inval("d_lut not 4-byte aligned");
+    mact_status st = check_access(*h, d_lut, "d_lut");
+    if (st != MACT_OK) return st;
     return cuda_status(launch_lut_build(*h, n, d_lut, (cudaStream_t)stream), "mact_lut_build launch");
 }
 
@@ -375,6 +444,13 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
     if (npix < 0 || npix > (int64_t(1) << 42)) return inval("pixel count out of range");
     if (npix == 0) return MACT_OK;
     if (!d_lut || !d_rgb || !d_out || !d_out[0] || !d_out[1] || !d_out[2]) return inval("NULL pointer");
+    if (!aligned4(d_lut) || !aligned4(d_out[0]) || !aligned4(d_out[1]) || !aligned4(d_out[2]) || !aligned4(d_sel))
+        return inval("d_lut, d_out[] and d_sel must be 4-byte aligned");
+    mact_status st = check_access(*h, d_lut, "d_lut");
+    if (st == MACT_OK) st = check_access(*h, d_rgb, "d_rgb");
+    for (int c = 0; c < 3 && st == MACT_OK; ++c) st = check_access(*h, d_out[c], "d_out");
+    if (st == MACT_OK) st = check_access(*h, d_sel, "d_sel");
+    if (st != MACT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (!lut_needs_pack(n))
         return cuda_status(launch_lut_interp(*h, method, d_lut, n, d_rgb, npix, d_out, d_sel, nullptr, s),
@@ -420,6 +496,9 @@ mact_status mact_lab_forward(mact_handle h, const float *d_x, int64_t nbatch, in
     if (st != MACT_OK) return st;
     if (nbatch * hw == 0) return MACT_OK;
     if (!d_x || !d_lab) return inval("NULL pointer");
+    if (!aligned4(d_x) || !aligned4(d_lab)) return inval("d_x and d_lab must be 4-byte aligned");
+    if ((st = check_access(*h, d_x, "d_x")) != MACT_OK || (st = check_access(*h, d_lab, "d_lab")) != MACT_OK)
+        return st;
     return cuda_status(launch_lab_forward(*h, d_x, nbatch, hw, d_lab, (cudaStream_t)stream), "mact_lab_forward");
 }
 
@@ -430,6 +509,11 @@ mact_status mact_lab_backward(mact_handle h, const float *d_x, const float *d_gr
     if (st != MACT_OK) return st;
     if (nbatch * hw == 0) return MACT_OK;
     if (!d_x || !d_grad_lab || !d_grad_x) return inval("NULL pointer");
+    if (!aligned4(d_x) || !aligned4(d_grad_lab) || !aligned4(d_grad_x))
+        return inval("float arrays must be 4-byte aligned");
+    if ((st = check_access(*h, d_x, "d_x")) != MACT_OK || (st = check_access(*h, d_grad_lab, "d_grad_lab")) != MACT_OK ||
+        (st = check_access(*h, d_grad_x, "d_grad_x")) != MACT_OK)
+        return st;
     return cuda_status(launch_lab_backward(*h, d_x, d_grad_lab, nbatch, hw, d_grad_x, (cudaStream_t)stream),
                        "mact_lab_backward");
 }
@@ -441,6 +525,12 @@ mact_status mact_lab_delta_e_loss(mact_handle h, const float *d_x, const float *
     if (st != MACT_OK) return st;
     if (nbatch * hw == 0) return inval("empty input: the mean is undefined");
     if (!d_x || !d_target_lab || !d_loss) return inval("NULL pointer");
+    if (!aligned4(d_x) || !aligned4(d_target_lab) || !aligned4(d_loss) || !aligned4(d_grad_x))
+        return inval("float arrays must be 4-byte aligned");
+    if ((st = check_access(*h, d_x, "d_x")) != MACT_OK ||
+        (st = check_access(*h, d_target_lab, "d_target_lab")) != MACT_OK ||
+        (st = check_access(*h, d_loss, "d_loss")) != MACT_OK || (st = check_access(*h, d_grad_x, "d_grad_x")) != MACT_OK)
+        return st;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lock(h->grad_mu);
     cudaError_t e = cudaSuccess;
@@ -474,6 +564,9 @@ mact_status mact_cube_error_lut(mact_handle h, int32_t method, const float *d_lu
     if (!h || !d_lut || !eps_avg || !eps_max) return inval("mact_cube_error_lut: NULL argument");
     if (method < MACT_TRILINEAR || method > MACT_TETRA) return inval("unknown interpolation method");
     if (n < 2 || n > 64) return inval("LUT size must be 2..64");
+    if (!aligned4(d_lut)) return inval("d_lut not 4-byte aligned");
+    mact_status st = check_access(*h, d_lut, "d_lut");
+    if (st != MACT_OK) return st;
     double out[2] = {0.0, 0.0};
     cudaStream_t s = nullptr;
     float4 *lut4 = nullptr;
@@ -495,6 +588,10 @@ mact_status mact_lut_cache_build(mact_handle h, const float *d_lut, int32_t n, f
     if (n < 2 || n > 64) return inval("LUT size must be 2..64");
     if (!d_lut || !d_cache) return inval("NULL pointer");
     if ((reinterpret_cast<uintptr_t>(d_cache) & 15) != 0) return inval("d_cache must be 16-byte aligned");
+    if (!aligned4(d_lut)) return inval("d_lut not 4-byte aligned");
+    mact_status st = check_access(*h, d_lut, "d_lut");
+    if (st == MACT_OK) st = check_access(*h, d_cache, "d_cache");
+    if (st != MACT_OK) return st;
     return cuda_status(launch_lut_cache_build(d_lut, n, reinterpret_cast<float4 *>(d_cache), (cudaStream_t)stream),
                        "mact_lut_cache_build");
 }
@@ -510,9 +607,22 @@ mact_status mact_lut_interp_cached(mact_handle h, int32_t method, const float *d
     if (npix == 0) return MACT_OK;
     if (!d_cache || !d_rgb || !d_out || !d_out[0] || !d_out[1] || !d_out[2]) return inval("NULL pointer");
     if ((reinterpret_cast<uintptr_t>(d_cache) & 15) != 0) return inval("d_cache must be 16-byte aligned");
+    if (!aligned4(d_out[0]) || !aligned4(d_out[1]) || !aligned4(d_out[2]) || !aligned4(d_sel))
+        return inval("d_out[] and d_sel must be 4-byte aligned");
+    mact_status st = check_access(*h, d_cache, "d_cache");
+    if (st == MACT_OK) st = check_access(*h, d_rgb, "d_rgb");
+    for (int c = 0; c < 3 && st == MACT_OK; ++c) st = check_access(*h, d_out[c], "d_out");
+    if (st == MACT_OK) st = check_access(*h, d_sel, "d_sel");
+    if (st != MACT_OK) return st;
     return cuda_status(launch_lut_interp_cached(*h, method, reinterpret_cast<const float4 *>(d_cache), n, d_rgb,
                                                 npix, d_out, d_sel, (cudaStream_t)stream),
                        "mact_lut_interp_cached");
+}
+
+int32_t mact_host_memory_access(mact_handle h)
+{
+    if (!h) return inval("mact_host_memory_access: NULL handle");
+    return h->any_host ? 1 : 0;
 }
 
 const char *mact_strerror(mact_status st)

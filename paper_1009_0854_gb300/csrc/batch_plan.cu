@@ -38,6 +38,7 @@ static mact_status plan_build(mact_handle h, const mact_image *imgs, int32_t cou
     if (!batch_cfg_supported(cfg)) { set_error("unsupported batch launch shape"); return MACT_E_UNSUPPORTED; }
     for (int32_t i = 0; i < count; ++i) {
         mact_status st = check_image(&imgs[i]);
+        if (st == MACT_OK) st = check_image_access(*h, imgs[i]);
         if (st != MACT_OK) return st;
     }
     std::vector<ImageDesc> list;

@@ -50,6 +50,14 @@ struct ImageDesc {
     int32_t dtype;
 };
 
+// A short work list carried in a kernel's parameter block (with the Coeffs
+// block it stays under the 4 KB classic parameter limit).
+constexpr int kParamImages = 32;
+struct ParamList {
+    ImageDesc img[kParamImages];
+};
+static_assert(sizeof(ParamList) + sizeof(Coeffs) + 64 <= 4096, "kernel parameters exceed 4 KB");
+
 // Horner evaluation a0 + x (a1 + x (a2 + ...)) with FMA, degree D.
 template <int D>
 __device__ __forceinline__ float horner(const float *a, float x)

@@ -34,6 +34,7 @@ struct TileShape {
     static constexpr int px = sub * SUBS;                // pixels per tile
     static constexpr int vpt = 3 * SUBS / 4;             // 16-byte input vectors per thread
     static constexpr int vecs = vpt * THREADS;           // 16-byte input vectors per tile
+    static constexpr int scratch = THREADS;              // 16-byte vectors of transpose scratch (shifted path)
 };
 
 template <int THREADS, int SUBS = kSubBlocks>
@@ -123,15 +124,61 @@ __device__ __forceinline__ void compute_full(const uint4 *sbuf, const Op &op, Ou
     }
 }
 
+// Full tile with 16-byte aligned input but output planes aligned only to
+// their element size (adjacent planes of W*H elements, W*H not a multiple of
+// 4): each warp passes its 128 values per plane through 512 bytes of shared
+// scratch, so that every warp store writes 32 consecutive elements instead of
+// four strided scalar stores per thread.  scr: THREADS*4 floats.
+template <int THREADS, int SUBS, typename OutT, class Op>
+__device__ __forceinline__ void compute_full_shifted(const uint4 *sbuf, float *scr, const Op &op, OutT *o0,
+                                                     OutT *o1, OutT *o2)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float *w = scr + 128 * warp;
+#pragma unroll(IsQuad<Op>::value ? 1 : SUBS)
+    for (int s = 0; s < SUBS; ++s) {
+        float v[3][4];
+        int sl[4];
+        apply4<THREADS>(sbuf, s, op, v, sl);
+        // this thread holds pixels wb + 4*lane + j of the warp's 128 (j < 4)
+        const int wb = s * TileShape<THREADS>::sub + 128 * warp;
+        OutT *dst[3] = {o0 + wb, o1 + wb, o2 + wb};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            __syncwarp();
+            *reinterpret_cast<float4 *>(w + 4 * lane) = make_float4(v[c][0], v[c][1], v[c][2], v[c][3]);
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) store1(dst[c] + lane + 32 * k, w[lane + 32 * k]);
+        }
+    }
+}
+
 // Guarded tile of cnt <= px pixels at any alignment.  Ends with a barrier
 // already passed after the staging; the caller synchronises before reusing
 // sbuf.
+// Stage nb input bytes into shared memory: 16-byte loads for the aligned
+// bulk when in is 16-byte aligned, single bytes otherwise and for the rest.
+template <int THREADS>
+__device__ __forceinline__ void stage_bytes(uint4 *sbuf, const uint8_t *in, int nb)
+{
+    uint8_t *sb = reinterpret_cast<uint8_t *>(sbuf);
+    int i0 = 0;
+    if ((reinterpret_cast<uintptr_t>(in) & 15) == 0) {
+        const int nv = nb >> 4;
+        const uint4 *p = reinterpret_cast<const uint4 *>(in);
+        for (int i = threadIdx.x; i < nv; i += THREADS) sbuf[i] = __ldcs(p + i);
+        i0 = nv << 4;
+    }
+    for (int i = i0 + threadIdx.x; i < nb; i += THREADS) sb[i] = in[i];
+}
+
 template <int THREADS, int SUBS, typename OutT, bool SEL, class Op>
 __device__ __forceinline__ void compute_guarded(uint4 *sbuf, const uint8_t *in, int cnt, const Op &op, OutT *o0,
                                                 OutT *o1, OutT *o2, int32_t *sel)
 {
-    uint8_t *sb = reinterpret_cast<uint8_t *>(sbuf);
-    for (int i = threadIdx.x; i < 3 * cnt; i += THREADS) sb[i] = in[i];
+    stage_bytes<THREADS>(sbuf, in, 3 * cnt);
     __syncthreads();
     for (int s = 0; s < SUBS; ++s) {
         const int p = s * TileShape<THREADS>::sub + kPxPerThread * threadIdx.x;
@@ -151,11 +198,48 @@ __device__ __forceinline__ void compute_guarded(uint4 *sbuf, const uint8_t *in, 
     }
 }
 
-// Tile t of image im (any geometry): the guarded or, when full and aligned,
-// the vector path.  The caller synchronises before reusing sbuf.
+// Partial tile (cnt < px pixels) with element-aligned outputs: staged like
+// the guarded path, stored through the warp transpose of the shifted path
+// with a bound on each element.  Whole warps stay together (the bound on a
+// warp's first pixel is warp-uniform); pixels past cnt are computed from
+// stale shared bytes and not stored.
+template <int THREADS, int SUBS, typename OutT, class Op>
+__device__ __forceinline__ void compute_tail_shifted(uint4 *sbuf, float *scr, const uint8_t *in, int cnt,
+                                                     const Op &op, OutT *o0, OutT *o1, OutT *o2)
+{
+    stage_bytes<THREADS>(sbuf, in, 3 * cnt);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float *w = scr + 128 * warp;
+    for (int s = 0; s < SUBS; ++s) {
+        const int wb = s * TileShape<THREADS>::sub + 128 * warp;
+        if (wb >= cnt) break;
+        float v[3][4];
+        int sl[4];
+        apply4<THREADS>(sbuf, s, op, v, sl);
+        OutT *dst[3] = {o0 + wb, o1 + wb, o2 + wb};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            __syncwarp();
+            *reinterpret_cast<float4 *>(w + 4 * lane) = make_float4(v[c][0], v[c][1], v[c][2], v[c][3]);
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = lane + 32 * k;
+                if (wb + i < cnt) store1(dst[c] + i, w[i]);
+            }
+        }
+    }
+}
+
+// Tile t of image im (any geometry): the vector path when full and aligned;
+// the shifted path when full with aligned input and element-aligned output
+// (scr given: THREADS*4 floats of shared scratch); else the guarded path.
+// The caller synchronises before reusing sbuf.
 template <int THREADS, typename OutT, bool SEL, class Op, int SUBS = kSubBlocks>
 __device__ __forceinline__ void process_tile(const ImageDesc &im, int64_t t, const Op &op, uint4 *sbuf,
-                                             int32_t *sel)
+                                             int32_t *sel, float *scr = nullptr)
 {
     constexpr int P = TileShape<THREADS, SUBS>::px;
     const uint32_t tpr = (uint32_t)im.tiles_per_row;     // < 2^31 (checked on the host)
@@ -174,13 +258,17 @@ __device__ __forceinline__ void process_tile(const ImageDesc &im, int64_t t, con
     uintptr_t oa = reinterpret_cast<uintptr_t>(o0) | reinterpret_cast<uintptr_t>(o1) |
                    reinterpret_cast<uintptr_t>(o2);
     if (SEL) oa |= reinterpret_cast<uintptr_t>(sl);
-    const bool fast = cnt == P && ((reinterpret_cast<uintptr_t>(in) & 15) == 0) && ((oa & omask) == 0);
-    if (fast) {
+    const bool full_in = cnt == P && ((reinterpret_cast<uintptr_t>(in) & 15) == 0);
+    const bool shifted = !SEL && scr != nullptr && (oa & (sizeof(OutT) - 1)) == 0;
+    if (full_in && ((oa & omask) == 0 || shifted)) {
         uint4 v[TileShape<THREADS, SUBS>::vpt];
         load_tile<THREADS, SUBS>(v, in);
         stage_tile<THREADS, SUBS>(sbuf, v);
         __syncthreads();
-        compute_full<THREADS, SUBS, OutT, SEL>(sbuf, op, o0, o1, o2, sl);
+        if ((oa & omask) == 0) compute_full<THREADS, SUBS, OutT, SEL>(sbuf, op, o0, o1, o2, sl);
+        else compute_full_shifted<THREADS, SUBS, OutT>(sbuf, scr, op, o0, o1, o2);
+    } else if (shifted) {
+        compute_tail_shifted<THREADS, SUBS, OutT>(sbuf, scr, in, cnt, op, o0, o1, o2);
     } else {
         compute_guarded<THREADS, SUBS, OutT, SEL>(sbuf, in, cnt, op, o0, o1, o2, sl);
     }
@@ -191,7 +279,7 @@ __device__ __forceinline__ void process_tile(const ImageDesc &im, int64_t t, con
 // guarded path; everything else walks tiles through process_tile.
 template <int THREADS, typename OutT, bool SEL, class Op, int SUBS = kSubBlocks>
 __device__ __forceinline__ void run_image(const ImageDesc &im, int64_t ntiles, const Op &op, uint4 *sbuf,
-                                          int32_t *sel)
+                                          int32_t *sel, float *scr = nullptr)
 {
     constexpr int P = TileShape<THREADS, SUBS>::px;
     if (streamable<OutT, SEL>(im, sel)) {
@@ -214,14 +302,18 @@ __device__ __forceinline__ void run_image(const ImageDesc &im, int64_t ntiles, c
         if (nfull < ntiles && blockIdx.x == (unsigned)(nfull % gridDim.x)) {
             __syncthreads();
             const int64_t o = P * nfull;
-            compute_guarded<THREADS, SUBS, OutT, SEL>(sbuf, im.rgb + 3 * o, (int)(im.width - o), op, b0 + o,
-                                                      b1 + o, b2 + o, SEL ? sel + o : nullptr);
+            if (!SEL && scr != nullptr)
+                compute_tail_shifted<THREADS, SUBS, OutT>(sbuf, scr, im.rgb + 3 * o, (int)(im.width - o), op, b0 + o,
+                                                          b1 + o, b2 + o);
+            else
+                compute_guarded<THREADS, SUBS, OutT, SEL>(sbuf, im.rgb + 3 * o, (int)(im.width - o), op, b0 + o,
+                                                          b1 + o, b2 + o, SEL ? sel + o : nullptr);
         }
         return;
     }
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         __syncthreads();
-        process_tile<THREADS, OutT, SEL, Op, SUBS>(im, t, op, sbuf, sel);
+        process_tile<THREADS, OutT, SEL, Op, SUBS>(im, t, op, sbuf, sel, scr);
     }
 }
 

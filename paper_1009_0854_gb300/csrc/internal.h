@@ -24,6 +24,10 @@ struct BatchCfg {
 struct mact_ctx {
     int device = 0;
     int num_sms = 0;
+    // 1: the device addresses any host memory through the host page tables,
+    // and pointers are not checked; 0: only device, pinned and registered host
+    // memory, checked before every launch
+    int any_host = 0;
     mact_config cfg{};
     mact::Coeffs co{};
     float *d_gamma = nullptr;            // 256 FP32 then 256 FP64 entries (Eq. equ_rgb_lin of each code)
@@ -66,6 +70,10 @@ cudaError_t launch_convert(const mact_ctx &h, const ImageDesc &im, cudaStream_t 
 cudaError_t launch_batch(const mact_ctx &h, const ImageDesc *d_imgs, int32_t count,
                          int64_t total_tiles, unsigned long long *d_counters, int grid,
                          cudaStream_t s, const BatchCfg &cfg = BatchCfg());
+// the same for at most kParamImages images, the list passed by value in the
+// kernel parameters (no device list, no counters)
+cudaError_t launch_batch_param(const mact_ctx &h, const ParamList &list, int32_t count, int64_t total_tiles,
+                               int grid, cudaStream_t s, const BatchCfg &cfg);
 int batch_blocks_per_sm(const mact_ctx &h, const BatchCfg &cfg = BatchCfg());
 bool batch_cfg_supported(const BatchCfg &cfg);
 
@@ -101,5 +109,10 @@ int64_t tiles_of(const ImageDesc &im);
 // tiles of tile_px pixels
 mact_status check_image(const mact_image *img);
 ImageDesc make_desc(const mact_image &img, int64_t tile_px = kTile);
+
+// api.cu: whether the kernels may dereference p (see mact_host_memory_access);
+// check_image_access applies it to an image's four pointers
+mact_status check_access(const mact_ctx &h, const void *p, const char *what);
+mact_status check_image_access(const mact_ctx &h, const mact_image &img);
 
 }  // namespace mact

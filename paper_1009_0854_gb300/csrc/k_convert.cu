@@ -38,10 +38,10 @@ k_image(const __grid_constant__ ImageDesc im, const __grid_constant__ Coeffs co,
         const float *__restrict__ gamma, int64_t ntiles)
 {
     __shared__ double sgam[256];
-    __shared__ uint4 sbuf[Shape::vecs];
+    __shared__ uint4 sbuf[Shape::vecs + Shape::scratch];
     load_table(TABLE, gamma, sgam);
     const Op op{reinterpret_cast<const float *>(sgam), co};
-    run_image<kThreads, OutT, false>(im, ntiles, op, sbuf, nullptr);
+    run_image<kThreads, OutT, false>(im, ntiles, op, sbuf, nullptr, reinterpret_cast<float *>(sbuf + Shape::vecs));
 }
 
 // HSI and SCT operators take no table; give them the same aggregate shape.
@@ -99,15 +99,16 @@ template <typename OutT, bool EXACT, bool RAT, int THREADS, int SUBS>
 __device__ __forceinline__ void batch_tile(const ImageDesc &im, int64_t t, const float *sgam,
                                            const Coeffs &co, uint4 *sbuf)
 {
+    float *scr = reinterpret_cast<float *>(sbuf + TileShape<THREADS, SUBS>::vecs);
     if (im.space == MACT_CIELAB) {
         const OpCielab<EXACT, RAT> op{sgam, co};
-        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr);
+        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr, scr);
     } else if (im.space == MACT_HSI) {
         const OpHsi<EXACT> op{co};
-        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr);
+        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr, scr);
     } else {
         const OpSct<EXACT> op{co};
-        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr);
+        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr, scr);
     }
 }
 
@@ -118,7 +119,7 @@ k_batch(const ImageDesc *__restrict__ imgs, int32_t count, int64_t total,
         const float *__restrict__ gamma)
 {
     __shared__ double sgam64[256];
-    __shared__ uint4 sbuf[TileShape<THREADS, SUBS>::vecs];
+    __shared__ uint4 sbuf[TileShape<THREADS, SUBS>::vecs + TileShape<THREADS, SUBS>::scratch];
     __shared__ long long s_tile;
     __shared__ int s_img;
     load_table((!EXACT && !RAT) ? kTable64 : kTable32, gamma, sgam64);
@@ -157,6 +158,34 @@ k_batch(const ImageDesc *__restrict__ imgs, int32_t count, int64_t total,
     }
 }
 
+// The same batched conversion for short lists, with the work list passed in
+// the kernel's parameter block instead of device memory: the launch needs no
+// copy and no device counter.  Tiles are uniform (all full but each image's
+// last), so CTAs take them grid-stride, t = blockIdx.x + k * gridDim.x.
+template <bool EXACT, bool RAT, int THREADS, int SUBS>
+__global__ void __launch_bounds__(THREADS)
+k_batch_param(const __grid_constant__ ParamList list, int32_t count, int64_t total,
+              const __grid_constant__ Coeffs co, const float *__restrict__ gamma)
+{
+    __shared__ double sgam64[256];
+    __shared__ uint4 sbuf[TileShape<THREADS, SUBS>::vecs + TileShape<THREADS, SUBS>::scratch];
+    load_table((!EXACT && !RAT) ? kTable64 : kTable32, gamma, sgam64);
+    const float *sgam = reinterpret_cast<const float *>(sgam64);
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+        __syncthreads();   // previous tile finished with sbuf
+        // last image whose first tile is <= t (the list is sorted by tile_begin)
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (list.img[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+        }
+        const ImageDesc &im = list.img[lo];
+        const int64_t lt = t - im.tile_begin;
+        if (im.dtype == MACT_F16) batch_tile<__half, EXACT, RAT, THREADS, SUBS>(im, lt, sgam, co, sbuf);
+        else batch_tile<float, EXACT, RAT, THREADS, SUBS>(im, lt, sgam, co, sbuf);
+    }
+}
+
 // Supported launch shapes (threads, sub-blocks): 16 to 32 pixels per thread,
 // tiles of 2048 to 8192 pixels.
 #define MACT_BATCH_SHAPES(X) X(128, 4) X(256, 4) X(512, 4) X(256, 8) X(128, 8)
@@ -174,9 +203,13 @@ static int occ_batch()
 {
     static int occ = 0;
     if (occ == 0) {
-        int o = 0;
+        int o = 0, op = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch<EXACT, RAT, THREADS, SUBS>,
                                                                       THREADS, 0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_batch_param<EXACT, RAT, THREADS, SUBS>,
+                                                              THREADS, 0);
+        if (op < o) o = op;   // one figure serves both forms
         occ = (e != cudaSuccess || o <= 0) ? 1 : o;
     }
     return occ;
@@ -209,6 +242,29 @@ static cudaError_t launch_shape(const mact_ctx &h, const ImageDesc *d_imgs, int3
     MACT_BATCH_SHAPES(MACT_LAUNCH)
 #undef MACT_LAUNCH
     return cudaErrorInvalidValue;
+}
+
+template <bool EXACT, bool RAT>
+static cudaError_t launch_shape_param(const mact_ctx &h, const ParamList &list, int32_t count, int64_t total,
+                                      int grid, cudaStream_t s, const BatchCfg &cfg)
+{
+#define MACT_LAUNCH(T, S)                                                                               \
+    if (cfg.threads == T && cfg.subs == S) {                                                            \
+        k_batch_param<EXACT, RAT, T, S><<<grid, T, 0, s>>>(list, count, total, h.co, h.d_gamma);        \
+        return cudaGetLastError();                                                                      \
+    }
+    MACT_BATCH_SHAPES(MACT_LAUNCH)
+#undef MACT_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch_param(const mact_ctx &h, const ParamList &list, int32_t count, int64_t total, int grid,
+                               cudaStream_t s, const BatchCfg &cfg)
+{
+    if (count < 1 || count > kParamImages) return cudaErrorInvalidValue;
+    if (h.cfg.exact) return launch_shape_param<true, true>(h, list, count, total, grid, s, cfg);
+    if (h.co.lab_rational) return launch_shape_param<false, true>(h, list, count, total, grid, s, cfg);
+    return launch_shape_param<false, false>(h, list, count, total, grid, s, cfg);
 }
 
 cudaError_t launch_batch(const mact_ctx &h, const ImageDesc *d_imgs, int32_t count, int64_t total,

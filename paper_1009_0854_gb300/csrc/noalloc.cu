@@ -74,6 +74,7 @@ extern "C" mact_status mact_convert_batch_static(mact_handle h, const mact_image
     }
     for (int32_t i = 0; i < count; ++i) {
         mact_status st = check_image(&imgs[i]);
+        if (st == MACT_OK) st = check_image_access(*h, imgs[i]);
         if (st != MACT_OK) return st;
     }
     cudaStream_t s = (cudaStream_t)stream;

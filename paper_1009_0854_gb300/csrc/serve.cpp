@@ -2,7 +2,11 @@
 // batching over one GPU.
 //
 // Requests (one image each, host or device buffers, any space and dtype)
-// are queued by mact_serve_submit.  One scheduler thread repeats a tick:
+// are queued by mact_serve_submit.  Host buffers the kernel can address
+// (pinned; any host memory where the device walks the host page tables) are
+// read and written in place by the kernel in direct mode (the default); the
+// others, and all host buffers in staged mode, go through a device staging
+// arena.  One scheduler thread repeats a tick:
 //   1. admit queued requests in arrival order while a slot is free and the
 //      device staging arena (the memory budget, allocated once at create)
 //      has room for the request's staged input and output;
@@ -12,7 +16,8 @@
 //      work-list kernel, then copy host outputs back on the D2H stream;
 //   3. retire requests whose completion event has fired (latency = submit
 //      to completion seen by the scheduler), release their slot and arena
-//      range.
+//      range; the events fire in admission order, so only the oldest is
+//      queried.
 // Requests that arrive while earlier ones are on the GPU are admitted in the
 // next tick, so copies of one batch overlap the kernel of another
 // (iteration-level continuous batching).  Nothing waits on the device
@@ -24,6 +29,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -43,16 +49,31 @@ double ms_since(Clock::time_point a, Clock::time_point b)
 
 enum ReqState { kQueued = 0, kInFlight = 1, kDone = 2, kFailed = 3, kCancelled = 4 };
 
+// Timing events of one tick's batch, shared by its requests: start (on the
+// H2D stream, before the batch's input copies), in (after them), comp (after
+// the kernel, on the compute stream).
+struct BatchEvents {
+    cudaEvent_t start = nullptr, in = nullptr, comp = nullptr;
+    ~BatchEvents()
+    {
+        if (start) cudaEventDestroy(start);
+        if (in) cudaEventDestroy(in);
+        if (comp) cudaEventDestroy(comp);
+    }
+};
+
 struct Request {
     uint64_t ticket = 0;
     mact_image img{};          // as submitted
-    bool in_host = false, out_host = false;
+    bool in_host = false, out_host = false;   // staged through the arena (else read/written in place)
     size_t in_bytes = 0, out_bytes = 0, elem = 4;
     size_t off = 0, len = 0;   // arena range
     uint8_t *d_in = nullptr;
     void *d_out[3] = {nullptr, nullptr, nullptr};
-    cudaEvent_t ev_done = nullptr;
-    Clock::time_point t_submit, t_done;
+    cudaEvent_t ev_out = nullptr;      // before the request's output copies (D2H stream)
+    cudaEvent_t ev_done = nullptr;     // after them
+    std::shared_ptr<BatchEvents> bev;
+    Clock::time_point t_submit, t_admit, t_done;
     int state = kQueued;
     int64_t pixels = 0;
 };
@@ -104,14 +125,18 @@ private:
     size_t size_ = 0;
 };
 
-bool is_host_pointer(const void *p)
+enum PtrKind { kDevice = 0, kPinned = 1, kPageable = 2 };
+
+PtrKind pointer_kind(const void *p)
 {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();   // clear: unknown pointers are pageable host memory
-        return true;
+        return kPageable;
     }
-    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+    if (a.type == cudaMemoryTypeUnregistered) return kPageable;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer == p ? kPinned : kPageable;
+    return kDevice;
 }
 
 }  // namespace
@@ -125,6 +150,7 @@ struct mact_server {
     int device = 0;
     size_t budget = 0;
     int max_slots = 0;
+    int mode = MACT_SERVE_DIRECT;          // how host buffers of new requests are used
     void *arena_base = nullptr;
     Arena arena;
     cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
@@ -133,14 +159,19 @@ struct mact_server {
     std::condition_variable cv_work;     // submit -> scheduler
     std::condition_variable cv_done;     // scheduler -> waiters
     std::deque<Request *> queue;
-    std::vector<Request *> inflight;
+    std::deque<Request *> inflight;      // admission order = completion order (one D2H stream)
     std::map<uint64_t, Request *> reqs;
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread worker;
 
-    // statistics over retired requests
+    // statistics over retired requests: submit-to-completion latency, and its
+    // stages (admission wait on the host; on the device, the batch's input
+    // copies, then kernel including its wait for the compute stream, then the
+    // request's output copy including its wait for earlier output copies)
     std::vector<double> latencies;
+    std::vector<double> st_queue, st_h2d, st_comp, st_d2h;
+    double d2h_bytes = 0.0, d2h_busy_ms = 0.0;   // output copies to host: bytes, summed copy time
     int64_t pixels_done = 0, batches = 0, failed = 0;
     Clock::time_point t_first, t_last;
     bool any_done = false;
@@ -171,6 +202,7 @@ static bool serve_tick(mact_server *s)
             r->off = off;
             r->len = r->in_bytes + r->out_bytes;
             r->state = kInFlight;
+            r->t_admit = Clock::now();
             batch.push_back(r);
         }
     }
@@ -179,7 +211,11 @@ static bool serve_tick(mact_server *s)
         // stage pointers and H2D copies
         std::vector<mact_image> imgs;
         imgs.reserve(batch.size());
-        cudaError_t e = cudaSuccess;
+        auto bev = std::make_shared<BatchEvents>();
+        cudaError_t e = cudaEventCreate(&bev->start);
+        if (e == cudaSuccess) e = cudaEventCreate(&bev->in);
+        if (e == cudaSuccess) e = cudaEventCreate(&bev->comp);
+        if (e == cudaSuccess) e = cudaEventRecord(bev->start, s->s_h2d);
         for (Request *r : batch) {
             uint8_t *base = static_cast<uint8_t *>(s->arena_base) + r->off;
             mact_image im = r->img;
@@ -207,19 +243,18 @@ static bool serve_tick(mact_server *s)
             }
             imgs.push_back(im);
         }
-        cudaEvent_t ev_in = nullptr, ev_comp = nullptr;
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_comp, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventRecord(ev_in, s->s_h2d);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->s_comp, ev_in, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(bev->in, s->s_h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->s_comp, bev->in, 0);
         mact_status st = MACT_OK;
         if (e == cudaSuccess) st = mact_convert_batch(s->h, imgs.data(), (int32_t)imgs.size(), s->s_comp);
-        if (e == cudaSuccess && st == MACT_OK) e = cudaEventRecord(ev_comp, s->s_comp);
-        if (e == cudaSuccess && st == MACT_OK) e = cudaStreamWaitEvent(s->s_d2h, ev_comp, 0);
+        if (e == cudaSuccess && st == MACT_OK) e = cudaEventRecord(bev->comp, s->s_comp);
+        if (e == cudaSuccess && st == MACT_OK) e = cudaStreamWaitEvent(s->s_d2h, bev->comp, 0);
         for (Request *r : batch) {
             if (e != cudaSuccess || st != MACT_OK) break;
             const mact_image &im = r->img;
             const int64_t W = im.width, H = im.height;
+            if (e == cudaSuccess) e = cudaEventCreate(&r->ev_out);
+            if (e == cudaSuccess) e = cudaEventRecord(r->ev_out, s->s_d2h);
             if (r->out_host) {
                 const size_t dp = H == 1 ? (size_t)W * r->elem : (size_t)im.out_pitch_elems * r->elem;
                 const size_t row = (size_t)W * r->elem;
@@ -238,16 +273,19 @@ static bool serve_tick(mact_server *s)
                     }
                 }
             }
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev_done, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreate(&r->ev_done);
             if (e == cudaSuccess) e = cudaEventRecord(r->ev_done, s->s_d2h);
+            r->bev = bev;
         }
-        if (ev_in) cudaEventDestroy(ev_in);
-        if (ev_comp) cudaEventDestroy(ev_comp);
         std::unique_lock<std::mutex> lk(s->mu);
         s->batches++;
         for (Request *r : batch) {
             if (e != cudaSuccess || st != MACT_OK || !r->ev_done) {
                 fail_locked(s, r, "serve", e);
+                if (r->ev_out) cudaEventDestroy(r->ev_out);
+                if (r->ev_done) cudaEventDestroy(r->ev_done);
+                r->ev_out = r->ev_done = nullptr;
+                r->bev.reset();
                 s->arena.release(r->off, r->len);
                 if (e != cudaSuccess) set_error(std::string("mact_serve: ") + cudaGetErrorString(e));
             } else {
@@ -256,17 +294,34 @@ static bool serve_tick(mact_server *s)
         }
         if (e != cudaSuccess || st != MACT_OK) s->cv_done.notify_all();
     }
-    // retire
+    // retire: every request's completion event is recorded on the one D2H
+    // stream, so they fire in admission order; query the oldest only
     std::unique_lock<std::mutex> lk(s->mu);
     bool retired = false;
-    for (size_t i = 0; i < s->inflight.size();) {
-        Request *r = s->inflight[i];
+    while (!s->inflight.empty()) {
+        Request *r = s->inflight.front();
         cudaError_t q = cudaEventQuery(r->ev_done);
-        if (q == cudaErrorNotReady) { ++i; continue; }
+        if (q == cudaErrorNotReady) break;
         r->t_done = Clock::now();
         if (q == cudaSuccess) {
             r->state = kDone;
             s->latencies.push_back(ms_since(r->t_submit, r->t_done));
+            float h2d = 0.0f, comp = 0.0f, d2h = 0.0f, copy = 0.0f;
+            if (r->bev && cudaEventElapsedTime(&h2d, r->bev->start, r->bev->in) == cudaSuccess &&
+                cudaEventElapsedTime(&comp, r->bev->in, r->bev->comp) == cudaSuccess &&
+                cudaEventElapsedTime(&d2h, r->bev->comp, r->ev_done) == cudaSuccess &&
+                cudaEventElapsedTime(&copy, r->ev_out, r->ev_done) == cudaSuccess) {
+                s->st_queue.push_back(ms_since(r->t_submit, r->t_admit));
+                s->st_h2d.push_back(h2d);
+                s->st_comp.push_back(comp);
+                s->st_d2h.push_back(d2h);
+                if (r->out_host) {
+                    s->d2h_bytes += (double)r->out_bytes;
+                    s->d2h_busy_ms += copy;
+                }
+            } else {
+                cudaGetLastError();
+            }
             s->pixels_done += r->pixels;
             if (!s->any_done) { s->t_first = r->t_submit; s->any_done = true; }
             s->t_last = r->t_done;
@@ -275,9 +330,11 @@ static bool serve_tick(mact_server *s)
         }
         cudaEventDestroy(r->ev_done);
         r->ev_done = nullptr;
+        if (r->ev_out) cudaEventDestroy(r->ev_out);
+        r->ev_out = nullptr;
+        r->bev.reset();
         s->arena.release(r->off, r->len);
-        s->inflight[i] = s->inflight.back();
-        s->inflight.pop_back();
+        s->inflight.pop_front();
         retired = true;
     }
     if (retired) s->cv_done.notify_all();
@@ -335,6 +392,15 @@ mact_status mact_serve_create(mact_handle h, size_t mem_budget_bytes, int32_t ma
     return MACT_OK;
 }
 
+mact_status mact_serve_set_mode(mact_server_t s, int32_t mode)
+{
+    if (!s) { set_error("mact_serve_set_mode: NULL server"); return MACT_E_INVAL; }
+    if (mode != MACT_SERVE_DIRECT && mode != MACT_SERVE_STAGED) { set_error("unknown serve mode"); return MACT_E_INVAL; }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->mode = mode;
+    return MACT_OK;
+}
+
 mact_status mact_serve_submit(mact_server_t s, const mact_image *img, uint64_t *ticket)
 {
     if (!s || !img || !ticket) { set_error("mact_serve_submit: NULL argument"); return MACT_E_INVAL; }
@@ -346,13 +412,29 @@ mact_status mact_serve_submit(mact_server_t s, const mact_image *img, uint64_t *
     r->elem = img->dtype == MACT_F16 ? 2 : 4;
     r->pixels = img->width * img->height;
     if (r->pixels > 0) {
-        r->in_host = is_host_pointer(img->rgb);
-        r->out_host = is_host_pointer(img->out[0]);
-        if (r->out_host != is_host_pointer(img->out[1]) || r->out_host != is_host_pointer(img->out[2])) {
+        const PtrKind kin = pointer_kind(img->rgb);
+        const PtrKind kout = pointer_kind(img->out[0]);
+        if ((kout == kDevice) != (pointer_kind(img->out[1]) == kDevice) ||
+            (kout == kDevice) != (pointer_kind(img->out[2]) == kDevice)) {
             delete r;
             set_error("mact_serve_submit: output planes must all be on the host or all on the device");
             return MACT_E_INVAL;
         }
+        // host memory is staged through the arena unless the kernel can
+        // address it in place and the server runs in direct mode
+        int mode;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            mode = s->mode;
+        }
+        auto staged = [&](PtrKind k) {
+            if (k == kDevice) return false;
+            if (mode == MACT_SERVE_STAGED) return true;
+            return k == kPageable && !s->h->any_host;
+        };
+        r->in_host = staged(kin);
+        r->out_host = false;
+        for (int c = 0; c < 3; ++c) r->out_host = r->out_host || staged(pointer_kind(img->out[c]));
     }
     r->in_bytes = r->in_host ? (size_t)(3 * r->pixels) : 0;
     r->out_bytes = r->out_host ? (size_t)(3 * r->pixels) * r->elem : 0;
@@ -443,6 +525,22 @@ mact_status mact_serve_stats(mact_server_t s, mact_serve_stats_t *out)
     if (!s || !out) { set_error("mact_serve_stats: NULL argument"); return MACT_E_INVAL; }
     std::lock_guard<std::mutex> lk(s->mu);
     std::memset(out, 0, sizeof(*out));
+    auto pct = [](std::vector<double> v, double p) {
+        if (v.empty()) return 0.0;
+        std::sort(v.begin(), v.end());
+        size_t k = (size_t)std::min<double>(v.size() - 1, std::max(0.0, p * (v.size() - 1) + 0.5));
+        return v[k];
+    };
+    out->queue_p50_ms = pct(s->st_queue, 0.50);
+    out->h2d_p50_ms = pct(s->st_h2d, 0.50);
+    out->compute_p50_ms = pct(s->st_comp, 0.50);
+    out->d2h_p50_ms = pct(s->st_d2h, 0.50);
+    out->queue_p99_ms = pct(s->st_queue, 0.99);
+    out->h2d_p99_ms = pct(s->st_h2d, 0.99);
+    out->compute_p99_ms = pct(s->st_comp, 0.99);
+    out->d2h_p99_ms = pct(s->st_d2h, 0.99);
+    out->d2h_copy_gbs = s->d2h_busy_ms > 0 ? s->d2h_bytes / (s->d2h_busy_ms * 1e-3) / 1e9 : 0.0;
+    out->d2h_busy_ms = s->d2h_busy_ms;
     std::vector<double> l = s->latencies;
     out->completed = (int64_t)l.size();
     out->failed = s->failed;
@@ -452,12 +550,8 @@ mact_status mact_serve_stats(mact_server_t s, mact_serve_stats_t *out)
     out->pixels = s->pixels_done;
     if (!l.empty()) {
         std::sort(l.begin(), l.end());
-        auto pct = [&l](double p) {
-            size_t k = (size_t)std::min<double>(l.size() - 1, std::max(0.0, p * (l.size() - 1) + 0.5));
-            return l[k];
-        };
-        out->p50_ms = pct(0.50);
-        out->p99_ms = pct(0.99);
+        out->p50_ms = pct(l, 0.50);
+        out->p99_ms = pct(l, 0.99);
         out->max_ms = l.back();
         const double span = ms_since(s->t_first, s->t_last);
         out->gpix_per_s = span > 0 ? (double)s->pixels_done / (span * 1e-3) / 1e9 : 0.0;

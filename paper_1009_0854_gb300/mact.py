@@ -20,6 +20,12 @@ DTYPES = {torch.float32: 0, torch.float16: 1}
 METHODS = {"trilinear": 0, "prism": 1, "pyramid": 2, "tetra": 3}
 
 MACT_OK = 0
+MACT_E_INVAL = -1
+MACT_E_NOMEM = -2
+MACT_E_CUDA = -3
+MACT_E_UNSUPPORTED = -4
+MACT_E_TIMEOUT = -5
+MACT_E_BUSY = -6
 
 
 class MactError(RuntimeError):
@@ -56,7 +62,12 @@ class ServeStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("in_flight", ctypes.c_int64), ("pixels", ctypes.c_int64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("gpix_per_s", ctypes.c_double)]
+                ("gpix_per_s", ctypes.c_double),
+                ("queue_p50_ms", ctypes.c_double), ("h2d_p50_ms", ctypes.c_double),
+                ("compute_p50_ms", ctypes.c_double), ("d2h_p50_ms", ctypes.c_double),
+                ("queue_p99_ms", ctypes.c_double), ("h2d_p99_ms", ctypes.c_double),
+                ("compute_p99_ms", ctypes.c_double), ("d2h_p99_ms", ctypes.c_double),
+                ("d2h_busy_ms", ctypes.c_double), ("d2h_copy_gbs", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,6 +108,8 @@ def lib():
         L.mact_serve_release.argtypes = [_VP, ctypes.c_uint64]
         L.mact_serve_stats.argtypes = [_VP, ctypes.POINTER(ServeStats)]
         L.mact_serve_destroy.argtypes = [_VP, ctypes.c_double]
+        L.mact_serve_set_mode.argtypes = [_VP, ctypes.c_int32]
+        L.mact_serve_set_mode.restype = ctypes.c_int
         for name in ("mact_serve_create", "mact_serve_submit", "mact_serve_poll", "mact_serve_wait",
                      "mact_serve_cancel", "mact_serve_release", "mact_serve_stats", "mact_serve_destroy"):
             getattr(L, name).restype = ctypes.c_int
@@ -132,6 +145,8 @@ def lib():
         L.mact_strerror.restype = ctypes.c_char_p
         L.mact_last_error.argtypes = []
         L.mact_last_error.restype = ctypes.c_char_p
+        L.mact_host_memory_access.argtypes = [_VP]
+        L.mact_host_memory_access.restype = ctypes.c_int32
         for name in ("mact_create", "mact_destroy", "mact_convert", "mact_convert_batch", "mact_convert_batch_static",
                      "mact_lut_build", "mact_lut_interp"):
             getattr(L, name).restype = ctypes.c_int
@@ -229,7 +244,8 @@ def _image(rgb, space, out):
 def mact_convert(h, rgb, space="cielab", dtype=torch.float32, out=None, stream=None):
     """Convert one (H, W, 3) uint8 CUDA image; returns a (3, H, W) tensor."""
     if out is None:
-        out = torch.empty((3, rgb.shape[0], rgb.shape[1]), dtype=dtype, device=rgb.device)
+        out = torch.empty((3, rgb.shape[0], rgb.shape[1]), dtype=dtype, device=rgb.device,
+                          pin_memory=rgb.device.type == "cpu")
     img = _image(rgb, space, out)
     _check(lib().mact_convert(h.ptr, ctypes.byref(img), _stream(stream)), "mact_convert")
     return out
@@ -240,7 +256,8 @@ def mact_convert_batch(h, images, dtype=torch.float32, outs=None, stream=None):
     Returns the list of (3, H, W) outputs."""
     n = len(images)
     if outs is None:
-        outs = [torch.empty((3, r.shape[0], r.shape[1]), dtype=dtype, device=r.device) for r, _ in images]
+        outs = [torch.empty((3, r.shape[0], r.shape[1]), dtype=dtype, device=r.device,
+                         pin_memory=r.device.type == "cpu") for r, _ in images]
     arr = (Image * max(n, 1))()
     for i, ((rgb, space), out) in enumerate(zip(images, outs)):
         arr[i] = _image(rgb, space, out)
@@ -254,7 +271,8 @@ def mact_convert_batch_static(h, images, dtype=torch.float32, outs=None, stream=
     images).  Output tensors are still created here unless outs is given."""
     n = len(images)
     if outs is None:
-        outs = [torch.empty((3, r.shape[0], r.shape[1]), dtype=dtype, device=r.device) for r, _ in images]
+        outs = [torch.empty((3, r.shape[0], r.shape[1]), dtype=dtype, device=r.device,
+                         pin_memory=r.device.type == "cpu") for r, _ in images]
     arr = (Image * max(n, 1))()
     for i, ((rgb, space), out) in enumerate(zip(images, outs)):
         arr[i] = _image(rgb, space, out)
@@ -281,9 +299,11 @@ def mact_lut_interp(h, method, lut, rgb, out=None, sel=False, stream=None):
     n = lut.shape[0]
     npix = rgb.numel() // 3
     if out is None:
-        out = torch.empty((3, npix), dtype=torch.float32, device=rgb.device)
+        out = torch.empty((3, npix), dtype=torch.float32, device=rgb.device,
+                          pin_memory=rgb.device.type == "cpu")
     ptrs = (_VP * 3)(*(out[c].data_ptr() for c in range(3)))
-    s = torch.empty(npix, dtype=torch.int32, device=rgb.device) if sel else None
+    s = (torch.empty(npix, dtype=torch.int32, device=rgb.device, pin_memory=rgb.device.type == "cpu")
+         if sel else None)
     m = METHODS[method] if isinstance(method, str) else int(method)
     _check(lib().mact_lut_interp(h.ptr, m, _VP(lut.data_ptr()), n, _VP(rgb.data_ptr()), npix,
                                  ctypes.byref(ptrs), _VP(s.data_ptr() if s is not None else 0),
@@ -320,7 +340,8 @@ def _image_array(images, outs):
 
 
 def _default_outs(images, dtype):
-    return [torch.empty((3, r.shape[0], r.shape[1]), dtype=dtype, device=r.device) for r, _ in images]
+    return [torch.empty((3, r.shape[0], r.shape[1]), dtype=dtype, device=r.device,
+                         pin_memory=r.device.type == "cpu") for r, _ in images]
 
 
 class BatchPlan:
@@ -453,6 +474,16 @@ def mact_serve_create(h, mem_budget_bytes, max_slots=64):
     return Server(p, h)
 
 
+SERVE_MODES = {"direct": 0, "staged": 1}
+
+
+def mact_serve_set_mode(srv, mode):
+    """'direct' (host buffers the kernel can address are used in place) or
+    'staged' (every host buffer is copied through the device arena)."""
+    m = SERVE_MODES[mode] if isinstance(mode, str) else int(mode)
+    _check(lib().mact_serve_set_mode(srv.ptr, m), "mact_serve_set_mode")
+
+
 def mact_serve_submit(srv, rgb, space="cielab", out=None, dtype=torch.float32):
     """Queue one (H, W, 3) uint8 image; rgb and out may be host (pinned or
     pageable) or CUDA tensors.  Returns (ticket, out)."""
@@ -515,14 +546,26 @@ def mact_lut_interp_cached(h, method, cache, n, rgb, out=None, sel=False, stream
         raise ValueError("rgb must be a contiguous (..., 3) uint8 tensor")
     npix = rgb.numel() // 3
     if out is None:
-        out = torch.empty((3, npix), dtype=torch.float32, device=rgb.device)
+        out = torch.empty((3, npix), dtype=torch.float32, device=rgb.device,
+                          pin_memory=rgb.device.type == "cpu")
     ptrs = (_VP * 3)(*(out[c].data_ptr() for c in range(3)))
-    s = torch.empty(npix, dtype=torch.int32, device=rgb.device) if sel else None
+    s = (torch.empty(npix, dtype=torch.int32, device=rgb.device, pin_memory=rgb.device.type == "cpu")
+         if sel else None)
     m = METHODS[method] if isinstance(method, str) else int(method)
     _check(lib().mact_lut_interp_cached(h.ptr, m, _VP(cache.data_ptr()), n, _VP(rgb.data_ptr()), npix,
                                         ctypes.byref(ptrs), _VP(s.data_ptr() if s is not None else 0),
                                         _stream(stream)), "mact_lut_interp_cached")
     return (out, s) if sel else out
+
+
+def mact_host_memory_access(h):
+    """1 if the kernels of h may be given any host memory (the device walks
+    the host page tables), 0 if only device and pinned/registered host memory
+    (other host pointers are then rejected before launch)."""
+    r = lib().mact_host_memory_access(h.ptr)
+    if r < 0:
+        _check(r, "mact_host_memory_access")
+    return r
 
 
 def mact_strerror(status):

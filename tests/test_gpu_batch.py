@@ -82,3 +82,37 @@ def test_unsupported_shape_rejected():
     with pytest.raises(mact.MactError) as e:
         mact.mact_set_batch_shape(h, 96, 16, 0)
     assert e.value.status == -4
+
+
+def test_short_list_by_value_equals_device_list(imgs):
+    """Up to 32 non-empty images travel in the kernel parameters, more go
+    through the device work list: both give each image's mact_convert result,
+    bit for bit, with empty images anywhere in the list."""
+    h = mact.mact_create()
+    empty = (torch.empty((0, 7, 3), dtype=torch.uint8, device="cuda"), "hsi")
+    more = imgs + imgs[:3]                                  # 33 non-empty
+    short = [empty] + more[:16] + [empty] + more[16:32]     # 32 non-empty + 2 empty
+    out_short = mact.mact_convert_batch(h, short)
+    out_long = mact.mact_convert_batch(h, more)
+    torch.cuda.synchronize()
+    got_short = [o for (r, _), o in zip(short, out_short) if r.shape[0] != 0]
+    assert len(got_short) == 32
+    for k, (rgb, space) in enumerate(more):
+        ref = mact.mact_convert(h, rgb, space)
+        torch.cuda.synchronize()
+        assert torch.equal(out_long[k], ref), k
+        if k < 32:
+            assert torch.equal(got_short[k], ref), k
+    outs = mact.mact_convert_batch(h, [empty, empty])       # nothing to launch
+    assert [tuple(o.shape) for o in outs] == [(3, 0, 7)] * 2
+
+
+@pytest.mark.parametrize("px_per_thread,threads", [(16, 128), (16, 512), (32, 256)])
+def test_short_list_every_shape(imgs, px_per_thread, threads):
+    h = mact.mact_create()
+    mact.mact_set_batch_shape(h, threads, px_per_thread, 0)
+    few = imgs[:5]
+    outs = mact.mact_convert_batch(h, few)
+    torch.cuda.synchronize()
+    for (rgb, space), o in zip(few, outs):
+        assert torch.equal(o, mact.mact_convert(h, rgb, space))

@@ -65,11 +65,13 @@ def test_each_result_same_alone_and_in_the_mix(h):
 
 
 def test_admission_respects_the_budget(h):
-    """A budget that holds one 512x512 FP32 request (0.75 + 3 MB) at a time:
-    all requests complete, one after another; a request larger than the whole
-    budget is refused at submit with MACT_E_NOMEM."""
+    """Staged mode, with a budget that holds one 512x512 FP32 request
+    (0.75 + 3 MB) at a time: all requests complete, one after another; a
+    request larger than the whole budget is refused at submit with
+    MACT_E_NOMEM.  In direct mode the same pinned request needs no budget."""
     im = synth.gradient_noise_image(512, 512, seed=1)
     srv = mact.mact_serve_create(h, 4 << 20, max_slots=8)
+    mact.mact_serve_set_mode(srv, "staged")
     ref = mact.mact_convert(h, torch.from_numpy(im).cuda(), "cielab").cpu()
     ts = [mact.mact_serve_submit(srv, torch.from_numpy(im).pin_memory(), "cielab") for _ in range(6)]
     for t, out in ts:
@@ -81,6 +83,10 @@ def test_admission_respects_the_budget(h):
     assert e.value.status == -2
     st = mact.mact_serve_stats(srv)
     assert st["completed"] == 6 and st["batches"] == 6
+    mact.mact_serve_set_mode(srv, "direct")
+    t, out = mact.mact_serve_submit(srv, big, "cielab")
+    mact.mact_serve_wait(srv, t, 30000)
+    assert torch.equal(out, mact.mact_convert(h, big.cuda(), "cielab").cpu())
     srv.close()
 
 
@@ -132,3 +138,31 @@ def test_wait_times_out_and_destroy_drains(h):
         mact.mact_serve_wait(srv, ts[-1], 0.0)
     assert e.value.status in (-5,)
     assert srv.close(60000.0) == 0
+
+
+def test_direct_and_staged_modes_agree(h):
+    """Direct mode (host buffers used in place by the kernel) and staged mode
+    (copied through the arena) give the same bits; only staged mode copies
+    outputs back."""
+    reqs = _requests(5, 24)
+    refs = _reference(h, reqs)
+    for mode in ("staged", "direct"):
+        srv = mact.mact_serve_create(h, 256 << 20, max_slots=8)
+        mact.mact_serve_set_mode(srv, mode)
+        pending = []
+        for i, ((im, space, dt), ref) in enumerate(zip(reqs, refs)):
+            rgb = torch.from_numpy(im).pin_memory() if i % 2 == 0 else torch.from_numpy(im.copy())
+            t, out = mact.mact_serve_submit(srv, rgb, space, dtype=dt)   # out: pinned host
+            pending.append((t, out, ref))
+        for t, out, ref in pending:
+            mact.mact_serve_wait(srv, t, 60000)
+            assert torch.equal(out, ref)
+        st = mact.mact_serve_stats(srv)
+        assert st["completed"] == len(reqs)
+        if mode == "staged":
+            assert st["d2h_busy_ms"] > 0
+        else:
+            assert st["d2h_busy_ms"] == 0
+        with pytest.raises(mact.MactError):
+            mact.mact_serve_set_mode(srv, 7)
+        srv.close()
