@@ -128,12 +128,30 @@ __device__ __forceinline__ float4 f4fma(float4 a, float s, float4 c)
     return make_float4(fmaf(a.x, s, c.x), fmaf(a.y, s, c.y), fmaf(a.z, s, c.z), 0.f);
 }
 
-// Node fetch: shared memory, or the read-only global path.
-template <bool SMEM>
+// Node fetch: shared memory, or the read-only global path.  With NARROW a
+// node's padding float is not read (an 8-byte and a 4-byte load instead of
+// one 16-byte load): fewer live registers for the same values.  Measured on
+// GB300 it pays only for the pyramid (5 nodes, the most register-hungry
+// selection); the other methods keep the single 16-byte load.
+template <bool SMEM, bool NARROW = false>
 __device__ __forceinline__ float4 node(const float4 *p)
 {
-    if constexpr (SMEM) return *p;
-    else return __ldg(p);
+    if constexpr (!NARROW) {
+        if constexpr (SMEM) return *p;
+        else return __ldg(p);
+    } else {
+        const float *f = reinterpret_cast<const float *>(p);
+        float2 xy;
+        float z;
+        if constexpr (SMEM) {
+            xy = *reinterpret_cast<const float2 *>(f);
+            z = f[2];
+        } else {
+            xy = __ldg(reinterpret_cast<const float2 *>(f));
+            z = __ldg(f + 2);
+        }
+        return make_float4(xy.x, xy.y, z, 0.f);
+    }
 }
 
 // Node strides: compile-time for N > 0, runtime otherwise.
@@ -252,7 +270,7 @@ struct OpLut {
     {
         const float4 *cb = CACHED ? lut + (int64_t)q.rec * 8 : lut + q.base;
 #pragma unroll
-        for (int k = 0; k < K; ++k) nd[k] = node<SMEM>(cb + q.off[k]);
+        for (int k = 0; k < K; ++k) nd[k] = node<SMEM, METHOD == MACT_PYRAMID>(cb + q.off[k]);
     }
 
     // value from the loaded nodes: directly, or c000 + interpolated differences
@@ -393,7 +411,10 @@ static cudaError_t launch_sel(const mact_ctx &h, const ImageDesc &im, const floa
                               int32_t *sel, cudaStream_t s)
 {
     constexpr int T = SMEM ? kLutThreadsSmem : kThreads;
-    constexpr int MINB = SMEM ? 2 : 4;   // cap registers at 64 so 1024+ threads stay resident
+    // register caps: 64 (2 x 512 threads) for the shared-memory LUT; 80
+    // (3 x 256 threads) for the global one, where the 64 cap spilled and
+    // measured 5-8% slower
+    constexpr int MINB = SMEM ? 2 : 3;
     if (sel) return launch_interp<T, MINB, METHOD, N, SMEM, true>(h, im, lut, lut4, n, sel, s);
     return launch_interp<T, MINB, METHOD, N, SMEM, false>(h, im, lut, lut4, n, sel, s);
 }
