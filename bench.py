@@ -419,9 +419,21 @@ def run_batch_workload(args):
         ms_batch = t(lambda: mact.mact_convert_batch(h, imgs, outs=outs))
         ms_single = t(lambda: [mact.mact_convert(h, r, s, out=o) for (r, s), o in zip(imgs, outs)])
         ms_plain = t(lambda: [mact.mact_convert(he, r, s, out=o) for (r, s), o in zip(imgs, outs)])
+        # the same calls with the image descriptors marshalled once: the C
+        # entry points' own per-call cost, without the binding's per-call
+        # marshalling of 256 descriptors
+        import ctypes
+        arr = mact._image_array(imgs, outs)
+        st = mact._stream(None)
+        L = mact.lib()
+        singles = [ctypes.byref(arr[i]) for i in range(len(imgs))]
+        ms_batch_c = t(lambda: L.mact_convert_batch(h.ptr, arr, len(imgs), st))
+        ms_single_c = t(lambda: [L.mact_convert(h.ptr, p, st) for p in singles])
         bpp = 3 + 3 * (4 if dt == torch.float32 else 2)
         hbm, _ = peaks()
         out[name] = {"graph_gpix_s": round(npx / ms_graph / 1e6, 2), "batch_gpix_s": round(npx / ms_batch / 1e6, 2),
+                     "batch_c_gpix_s": round(npx / ms_batch_c / 1e6, 2),
+                     "per_image_c_gpix_s": round(npx / ms_single_c / 1e6, 2),
                      "per_image_mact_gpix_s": round(npx / ms_single / 1e6, 2),
                      "per_image_exact_gpix_s": round(npx / ms_plain / 1e6, 2),
                      "graph_hbm_frac": round(npx * bpp / (ms_graph * 1e-3) / 1e9 / hbm, 4),

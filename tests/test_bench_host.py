@@ -1,0 +1,86 @@
+"""Host-side logic of bench.py that needs no GPU: the pinned output ring of
+the serving load generator (no overlap between live slots, every slot in
+bounds, back-pressure that always makes progress) and the determinism of the
+serving trace."""
+import random
+
+import pytest
+
+import bench
+from paper_1009_0854_gb300 import synth
+
+
+class _FakeTensor:
+    def __init__(self, n):
+        self.n = n
+
+    def pin_memory(self):
+        return self
+
+    def numel(self):
+        return self.n
+
+    def __getitem__(self, sl):
+        return (sl.start, sl.stop)
+
+
+class _FakeTorch:
+    float32 = "float32"
+
+    @staticmethod
+    def empty(n, dtype=None):
+        return _FakeTensor(n)
+
+
+def _check_live(ring):
+    spans = sorted((e[0], e[0] + e[1]) for e in ring.live if not e[2])
+    for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+        assert a1 <= b0
+    for a0, a1 in spans:
+        assert 0 <= a0 and a1 <= ring.n
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ring_slots_never_overlap(seed):
+    ring = bench.PinnedRing(_FakeTorch, 1 << 20)
+    rng = random.Random(seed)
+    held = []
+    reclaims = [0]
+
+    def reclaim():
+        reclaims[0] += 1
+        ring.give(held.pop(0))
+
+    for _ in range(5000):
+        if held and (rng.random() < 0.45 or len(held) > 24):
+            e = held.pop(rng.randrange(len(held)) if rng.random() < 0.3 else 0)
+            ring.give(e)
+        else:
+            n = rng.randrange(1, 180000)
+            view, e = ring.take(n, reclaim)
+            assert view[1] - view[0] == n // 4
+            assert view[0] == e[0] // 4 and e[0] % bench.PinnedRing.ALIGN == 0
+            held.append(e)
+        _check_live(ring)
+    assert reclaims[0] > 0                   # back-pressure was exercised
+
+
+def test_ring_rejects_oversize_and_resets_when_empty():
+    ring = bench.PinnedRing(_FakeTorch, 4096)
+    with pytest.raises(MemoryError):
+        ring.take(8192, lambda: None)
+    _, e1 = ring.take(1000, None)
+    _, e2 = ring.take(1000, None)
+    ring.give(e2)
+    ring.give(e1)
+    assert not ring.live
+    _, e3 = ring.take(4000, None)            # whole ring again after a full release
+    assert e3[0] == 0
+
+
+def test_serve_trace_is_deterministic():
+    a = synth.serve_trace(rate=2000.0, duration=0.5, seed=3)
+    b = synth.serve_trace(rate=2000.0, duration=0.5, seed=3)
+    assert a == b
+    assert all(0 < t < 0.5 for t, *_ in a)
+    assert all(0.09e6 <= h * w <= 24.5e6 for _, h, w, _, _ in a)
