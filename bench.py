@@ -341,8 +341,15 @@ def cpu_baseline(npix):
     t = time.perf_counter()
     _oracle_rows(rgb, luts, cores)
     dt = time.perf_counter() - t
+    # one thread, for comparison with the paper's single-threaded timings
+    n1 = min(npix, 1 << 20)
+    t = time.perf_counter()
+    _oracle_rows(rgb[:n1], luts, 1)
+    dt1 = time.perf_counter() - t
     return {"value": round(len(ROWS) * npix / dt / 1e9, 6), "unit": "Gpix/s", "cores": cores, "kind": "oracle",
-            "sample": "first %d cube colours x %d conversions (%.1f s wall)" % (npix, len(ROWS), dt)}
+            "sample": "first %d cube colours x %d conversions (%.1f s wall)" % (npix, len(ROWS), dt),
+            "single_thread": {"value": round(len(ROWS) * n1 / dt1 / 1e9, 6), "unit": "Gpix/s", "cores": 1,
+                              "sample": "first %d cube colours x %d conversions (%.1f s wall)" % (n1, len(ROWS), dt1)}}
 
 
 def run_reference(args):
@@ -383,6 +390,46 @@ def run_reference(args):
 
 def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_large_workload(args):
+    """Single large images: the 512x512 parity generator (smooth gradients
+    over the upper half, uniform noise below) at 8192x8192 and 16384x16384,
+    MACT and exact CIELAB/HSI/SCT, FP32 and FP16 planes; inputs and outputs
+    are far larger than L2."""
+    import torch
+    from paper_1009_0854_gb300 import mact, synth
+    dev = torch.device("cuda", 0)
+    hbm, _ = peaks()
+    hm, he = mact.mact_create(), mact.mact_create(exact=1)
+    rows = {}
+    for side in (8192, 16384):
+        rgb = torch.from_numpy(synth.gradient_noise_image(side, side, seed=0)).to(dev)
+        npx = side * side
+        for dt, dname, bpp in ((torch.float32, "f32", 15), (torch.float16, "f16", 9)):
+            out = torch.empty((3, side, side), dtype=dt, device=dev)
+            for hname, h in (("mact", hm), ("exact", he)):
+                for space in ("cielab", "hsi", "sct"):
+                    fn = lambda: mact.mact_convert(h, rgb, space, out=out)      # noqa: E731
+                    for _ in range(3):
+                        fn()
+                    torch.cuda.synchronize()
+                    a, b = _events(torch)
+                    k = max(5, args.steps // 4)
+                    a.record()
+                    for _ in range(k):
+                        fn()
+                    b.record()
+                    torch.cuda.synchronize()
+                    ms = a.elapsed_time(b) / k
+                    rows["%d_%s_%s_%s" % (side, hname, space, dname)] = {
+                        "ms": round(ms, 4), "gpix_s": round(npx / ms / 1e6, 2),
+                        "gb_s": round(npx * bpp / ms / 1e6, 1), "hbm_frac": round(npx * bpp / ms / 1e6 / hbm, 4)}
+            del out
+        del rgb
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "large: 8192^2 and 16384^2 single images (gradients + noise), %d B/px FP32, "
+                      "%d B/px FP16, peak %.1f GB/s measured" % (15, 9, hbm), "rows": rows}))
 
 
 def run_batch_workload(args):
@@ -712,8 +759,32 @@ def run_serve_workload(args):
     served(warm_trace, "direct")
     served(warm_trace, "staged")
     plain(warm_trace)
+
+    def same_delta_e():
+        """Served results equal single-image conversions bit for bit (checked
+        on a sample of the trace's requests), so their max Delta E*ab is the
+        MACT transform's own: reported over the whole cube by the device error
+        kernels, beside the exact-libm path's."""
+        srv = mact.mact_serve_create(h, 1 << 30, max_slots=16)
+        same, k = True, 0
+        for ta, hgt, wid, _, space in trace[:: max(1, len(trace) // 24)][:24]:
+            rgb = req_in(hgt, wid)
+            tk, out = mact.mact_serve_submit(srv, rgb, space)
+            mact.mact_serve_wait(srv, tk, 60000)
+            ref = mact.mact_convert(h, rgb.to(dev), space).cpu()
+            torch.cuda.synchronize()
+            same = same and torch.equal(out, ref)
+            mact.mact_serve_release(srv, tk)
+            k += 1
+        srv.close()
+        e_mact = mact.mact_cube_error(h, "cielab")
+        e_exact = mact.mact_cube_error(mact.mact_create(exact=1), "cielab")
+        return {"sampled_requests": k, "served_bit_identical_to_single_image": same,
+                "mact_cielab_delta_e_max_cube": round(e_mact[1], 6),
+                "mact_cielab_delta_e_avg_cube": round(e_mact[0], 6),
+                "exact_fp32_cielab_delta_e_max_cube": round(e_exact[1], 8)}
     results = {"served_direct": served(trace, "direct"), "served_staged": served(trace, "staged"),
-               "plain_exact_per_image": plain(trace),
+               "plain_exact_per_image": plain(trace), "same_delta_e": same_delta_e(),
                "link": {"d2h_gbs_ring_spread": ring_gbs, "d2h_gbs_ring_start": ring0_gbs}}
     print(json.dumps({"workload": "serve: Poisson 2000 req/s for %g s, 0.1-24 Mpx, pinned host buffers"
                       % args.serve_seconds, "rows": results}))
@@ -729,7 +800,7 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=1 << 22)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cube", choices=["cube", "batch", "serve", "grad", "lut"],
+    ap.add_argument("--workload", default="cube", choices=["cube", "batch", "serve", "grad", "lut", "large"],
                     help="cube: the default step; the others measure the batched, served and "
                          "differentiable forms on their own workloads")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -745,6 +816,8 @@ def main():
         run_grad_workload(args)
     elif args.workload == "lut":
         run_lut_workload(args)
+    elif args.workload == "large":
+        run_large_workload(args)
     else:
         run_gpu(args)
 
