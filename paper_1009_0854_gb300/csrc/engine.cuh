@@ -73,36 +73,18 @@ __device__ __forceinline__ void stage_tile(uint4 *sbuf, const uint4 (&v)[TileSha
     for (int k = 0; k < TileShape<THREADS, SUBS>::vpt; ++k) sbuf[threadIdx.x + k * THREADS] = v[k];
 }
 
-// Operators evaluate one pixel (operator()); an operator that declares
-// kQuad = true instead evaluates the thread's 4 consecutive pixels together
-// (quad()), which lets it reuse work between neighbouring pixels.
-template <class Op, class = void>
-struct IsQuad {
-    static constexpr bool value = false;
-};
-template <class Op>
-struct IsQuad<Op, decltype(void(Op::kQuad))> {
-    static constexpr bool value = Op::kQuad;
-};
-
-// Apply op to the 4 pixels of sub-block s owned by this thread.
+// Apply op (one pixel per call: op(r, g, b, o0, o1, o2) returns an int id)
+// to the 4 pixels of sub-block s owned by this thread.
 template <int THREADS, class Op>
 __device__ __forceinline__ void apply4(const uint4 *sbuf, int s, const Op &op, float (&v)[3][4], int (&sl)[4])
 {
     const uint32_t *sw = reinterpret_cast<const uint32_t *>(sbuf) + s * 3 * THREADS + 3 * threadIdx.x;
     const uint32_t w0 = sw[0], w1 = sw[1], w2 = sw[2];
     // bytes: w0 = r0 g0 b0 r1 | w1 = g1 b1 r2 g2 | w2 = b2 r3 g3 b3
-    if constexpr (IsQuad<Op>::value) {
-        const uint32_t r[4] = {w0 & 255u, w0 >> 24, (w1 >> 16) & 255u, (w2 >> 8) & 255u};
-        const uint32_t g[4] = {(w0 >> 8) & 255u, w1 & 255u, w1 >> 24, (w2 >> 16) & 255u};
-        const uint32_t b[4] = {(w0 >> 16) & 255u, (w1 >> 8) & 255u, w2 & 255u, w2 >> 24};
-        op.quad(r, g, b, v, sl);
-    } else {
-        sl[0] = op(w0 & 255u, (w0 >> 8) & 255u, (w0 >> 16) & 255u, v[0][0], v[1][0], v[2][0]);
-        sl[1] = op(w0 >> 24, w1 & 255u, (w1 >> 8) & 255u, v[0][1], v[1][1], v[2][1]);
-        sl[2] = op((w1 >> 16) & 255u, w1 >> 24, w2 & 255u, v[0][2], v[1][2], v[2][2]);
-        sl[3] = op((w2 >> 8) & 255u, (w2 >> 16) & 255u, w2 >> 24, v[0][3], v[1][3], v[2][3]);
-    }
+    sl[0] = op(w0 & 255u, (w0 >> 8) & 255u, (w0 >> 16) & 255u, v[0][0], v[1][0], v[2][0]);
+    sl[1] = op(w0 >> 24, w1 & 255u, (w1 >> 8) & 255u, v[0][1], v[1][1], v[2][1]);
+    sl[2] = op((w1 >> 16) & 255u, w1 >> 24, w2 & 255u, v[0][2], v[1][2], v[2][2]);
+    sl[3] = op((w2 >> 8) & 255u, (w2 >> 16) & 255u, w2 >> 24, v[0][3], v[1][3], v[2][3]);
 }
 
 // Full, aligned tile: sbuf holds its input; outputs start at o* (+ sel).
@@ -110,8 +92,9 @@ template <int THREADS, int SUBS, typename OutT, bool SEL, class Op>
 __device__ __forceinline__ void compute_full(const uint4 *sbuf, const Op &op, OutT *o0, OutT *o1, OutT *o2,
                                              int32_t *sel)
 {
-    // quad operators (gathers with reuse) keep one sub-block live at a time
-#pragma unroll(IsQuad<Op>::value ? 1 : SUBS)
+    // an explicit count: a bare "#pragma unroll" here compiles to more
+    // registers (63 vs 48 for MACT CIELAB) and spills in the LUT kernels
+#pragma unroll(SUBS)
     for (int s = 0; s < SUBS; ++s) {
         float v[3][4];
         int sl[4];
@@ -136,7 +119,7 @@ __device__ __forceinline__ void compute_full_shifted(const uint4 *sbuf, float *s
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     float *w = scr + 128 * warp;
-#pragma unroll(IsQuad<Op>::value ? 1 : SUBS)
+#pragma unroll(SUBS)
     for (int s = 0; s < SUBS; ++s) {
         float v[3][4];
         int sl[4];

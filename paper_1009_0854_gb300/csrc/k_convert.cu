@@ -55,13 +55,12 @@ static cudaError_t launch_one(const mact_ctx &h, const ImageDesc &im, cudaStream
 {
     const int64_t nt = tiles_of(im);
     if (nt == 0) return cudaSuccess;
-    static int occ = 0;   // resident CTAs per SM of this instantiation
-    if (occ == 0) {
+    // resident CTAs per SM of this instantiation (thread-safe one-time init)
+    static const int occ = [] {
         int o = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_image<Op, OutT, GAMMA>,
-                                                                      kThreads, 0);
-        occ = (e != cudaSuccess || o <= 0) ? 1 : o;
-    }
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_image<Op, OutT, GAMMA>, kThreads, 0);
+        return (e != cudaSuccess || o <= 0) ? 1 : o;
+    }();
     const int64_t cap = (int64_t)h.num_sms * occ;
     const int64_t grid = nt < cap ? nt : cap;
     k_image<Op, OutT, GAMMA><<<(unsigned)grid, kThreads, 0, s>>>(im, h.co, h.d_gamma, nt);
@@ -201,8 +200,7 @@ bool batch_cfg_supported(const BatchCfg &cfg)
 template <bool EXACT, bool RAT, int THREADS, int SUBS>
 static int occ_batch()
 {
-    static int occ = 0;
-    if (occ == 0) {
+    static const int occ = [] {   // thread-safe one-time init
         int o = 0, op = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch<EXACT, RAT, THREADS, SUBS>,
                                                                       THREADS, 0);
@@ -210,8 +208,8 @@ static int occ_batch()
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_batch_param<EXACT, RAT, THREADS, SUBS>,
                                                               THREADS, 0);
         if (op < o) o = op;   // one figure serves both forms
-        occ = (e != cudaSuccess || o <= 0) ? 1 : o;
-    }
+        return (e != cudaSuccess || o <= 0) ? 1 : o;
+    }();
     return occ;
 }
 

@@ -4,11 +4,11 @@
 //
 // Extraction is bit-identical to an integer implementation: along each axis
 // s = v (n-1), idx = s div 255, rem = s mod 255, and the code v = 255 uses
-// idx = n-2, rem = 255; the fraction is rem/255.  Every CTA tabulates, per
-// 8-bit code and axis, the node offset idx * stride and the fraction, so a
-// pixel's cell costs three shared loads; simplex choices compare fractions,
-// which order exactly as the integer remainders do (x -> x/255 is strictly
-// increasing on the integers 0..255 in FP32).
+// idx = n-2, rem = 255; the fraction is rem * fl(1/255).  It is computed per
+// pixel in integer arithmetic (no extra shared loads: the interpolation's
+// gathers already keep the shared/L1 data pipe busy).  Simplex choices
+// compare fractions, which order exactly as the integer remainders do
+// (rem -> rem * fl(1/255) is strictly increasing on 0..255 in FP32).
 //
 // LUT placement: for n <= 17 every CTA stages the whole LUT in shared memory
 // as float4 nodes (17^3 x 16 B = 78.6 KB), so a node is one 16-byte shared
@@ -18,17 +18,14 @@
 // strides are compile-time constants, so node addresses are immediate
 // offsets from the cell's base.
 #include "engine.cuh"
+#include <atomic>
+
 #include "internal.h"
 
 namespace mact {
 
 constexpr int kLutSmemMaxN = 17;
 constexpr int kLutThreadsSmem = 512;
-// Cell extraction: false = integer arithmetic per pixel (div by 255 as a
-// multiply-shift), true = per-code tables in shared memory.  The gathers of
-// the interpolation already saturate the shared/L1 data pipe, so the
-// arithmetic form (no extra shared loads) is the default.
-constexpr bool kLocateByTable = false;
 
 // --------------------------------------------------------------- packing
 
@@ -101,26 +98,6 @@ cudaError_t launch_lut_cache_build(const float *d_lut, int n, float4 *d_cache, c
 
 // ---------------------------------------------------------- interpolation
 
-// Per-code extraction table entry: node offset along the axis and fraction.
-struct AxisEntry {
-    int off;
-    float f;
-};
-
-__device__ __forceinline__ void fill_axis_tables(AxisEntry *tab, int n)
-{
-    // tab[axis * 256 + v], axis 0 = R (stride n^2), 1 = G (n), 2 = B (1)
-    for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) {
-        const int axis = i >> 8, v = i & 255;
-        const int s = v * (n - 1);
-        int idx = s / 255, rem = s - 255 * idx;
-        if (idx == n - 1) { idx = n - 2; rem = 255; }
-        const int stride = axis == 0 ? n * n : (axis == 1 ? n : 1);
-        tab[i].off = idx * stride;
-        tab[i].f = (float)rem * (1.0f / 255.0f);
-    }
-}
-
 __device__ __forceinline__ float4 f4sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, 0.f); }
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, 0.f); }
 __device__ __forceinline__ float4 f4fma(float4 a, float s, float4 c)
@@ -186,14 +163,8 @@ struct Sel {
 // c000 + the interpolation of the differences).
 template <int METHOD, int N, bool SMEM, bool CACHED = false>
 struct OpLut {
-    // Per-pixel evaluation.  (A quad() form that reuses a cell's nodes across
-    // the thread's 4 pixels is kept, but disabled: the predicated reloads
-    // and the live node registers cost more than the gathers they save on
-    // every input measured -- coherent cube, smooth and noisy images.)
-    static constexpr bool kQuad = false;
     static constexpr int K = NodeCount<METHOD>::K;
     const float4 *lut;        // shared or global float4 nodes, or cell records
-    const AxisEntry *tab;     // shared extraction table
     Strides<N> st;
 
     __device__ __forceinline__ static void locate(uint32_t v, int n, int &idx, float &f)
@@ -213,19 +184,13 @@ struct OpLut {
         const int sR = CACHED ? 4 : st.r(), sG = CACHED ? 2 : st.g(), sB = 1;
         Sel<METHOD> q;
         float fr, fg, fb;
-        if (kLocateByTable) {
-            const AxisEntry er = tab[r], eg = tab[256 + g], eb = tab[512 + b];
-            q.base = er.off + eg.off + eb.off;
-            fr = er.f; fg = eg.f; fb = eb.f;
-        } else {
-            const int n = st.g();
-            int ir, ig, ib;
-            locate(r, n, ir, fr);
-            locate(g, n, ig, fg);
-            locate(b, n, ib, fb);
-            q.base = (ir * n + ig) * n + ib;
-            if (CACHED) q.rec = (ir * (n - 1) + ig) * (n - 1) + ib;
-        }
+        const int n = st.g();
+        int ir, ig, ib;
+        locate(r, n, ir, fr);
+        locate(g, n, ig, fg);
+        locate(b, n, ib, fb);
+        q.base = (ir * n + ig) * n + ib;
+        if (CACHED) q.rec = (ir * (n - 1) + ig) * (n - 1) + ib;
         if (METHOD == MACT_TRILINEAR) {
             const int o[8] = {0, sB, sG, sG + sB, sR, sR + sB, sR + sG, sR + sG + sB};
 #pragma unroll
@@ -330,29 +295,6 @@ struct OpLut {
         return q.base * 8 + q.simplex;
     }
 
-    // The thread's 4 consecutive pixels: nodes are read again only when the
-    // cell or the simplex changes from the previous pixel (neighbouring
-    // pixels of natural and synthetic images usually share both).
-    __device__ __forceinline__ void quad(const uint32_t (&r)[4], const uint32_t (&g)[4], const uint32_t (&b)[4],
-                                         float (&v)[3][4], int (&sl)[4]) const
-    {
-        float4 nd[K];
-        int prev = -1;
-#pragma unroll 1
-        for (int j = 0; j < 4; ++j) {
-            const Sel<METHOD> q = select(r[j], g[j], b[j]);
-            const int key = q.base * 8 + q.simplex;
-            if (key != prev) {
-                load(q, nd);
-                prev = key;
-            }
-            const float4 o = value(nd, q);
-            v[0][j] = o.x;
-            v[1][j] = o.y;
-            v[2][j] = o.z;
-            sl[j] = key;
-        }
-    }
 };
 
 // SMEM: stage the packed float3 LUT as float4 nodes in shared memory.
@@ -364,8 +306,6 @@ k_lut_interp(const __grid_constant__ ImageDesc im, const float *__restrict__ lut
 {
     extern __shared__ float4 slut[];
     __shared__ uint4 sbuf[TileShape<THREADS>::vecs];
-    __shared__ AxisEntry stab[kLocateByTable ? 3 * 256 : 1];
-    if (kLocateByTable) fill_axis_tables(stab, n);
     OpLut<METHOD, N, SMEM, CACHED> op;
     if constexpr (SMEM) {
         const int nodes = n * n * n;
@@ -375,7 +315,6 @@ k_lut_interp(const __grid_constant__ ImageDesc im, const float *__restrict__ lut
     } else {
         op.lut = lut4;
     }
-    op.tab = stab;
     op.st.n = n;
     run_image<THREADS, float, SEL>(im, ntiles, op, sbuf, sel);
 }
@@ -388,17 +327,27 @@ static cudaError_t launch_interp(const mact_ctx &h, const ImageDesc &im, const f
     if (nt == 0) return cudaSuccess;
     auto kern = k_lut_interp<THREADS, MINB, METHOD, N, SMEM, SEL, CACHED>;
     const size_t smem = SMEM ? (size_t)n * n * n * sizeof(float4) : 0;
-    static int occ_cache[kLutSmemMaxN + 1] = {0};
-    int &occ = occ_cache[SMEM ? n : 0];
-    if (occ == 0) {
-        if (SMEM) {
+    // The shared-memory attribute is per device: remember the devices it was
+    // set on.  Occupancy per LUT size (it depends on the staged LUT's bytes).
+    // Both caches are atomics: concurrent first launches compute the same value.
+    static std::atomic<uint64_t> attr_devices{0};
+    static std::atomic<int> occ_cache[kLutSmemMaxN + 1];
+    if (SMEM) {
+        const uint64_t bit = 1ull << (h.device & 63);
+        if ((attr_devices.load(std::memory_order_acquire) & bit) == 0) {
             const int maxs = kLutSmemMaxN * kLutSmemMaxN * kLutSmemMaxN * (int)sizeof(float4);
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
             if (e != cudaSuccess) return e;
+            attr_devices.fetch_or(bit, std::memory_order_acq_rel);
         }
+    }
+    std::atomic<int> &slot = occ_cache[SMEM ? n : 0];
+    int occ = slot.load(std::memory_order_relaxed);
+    if (occ == 0) {
         int o = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, THREADS, smem);
         occ = (e != cudaSuccess || o <= 0) ? 1 : o;
+        slot.store(occ, std::memory_order_relaxed);
     }
     const int64_t cap = (int64_t)h.num_sms * occ;
     const int64_t grid = nt < cap ? nt : cap;
