@@ -25,7 +25,15 @@
 namespace mact {
 
 constexpr int kLutSmemMaxN = 17;
-constexpr int kLutThreadsSmem = 512;
+// Threads per CTA of the shared-memory LUT kernels (two CTAs per SM, each
+// with its own staged copy of the LUT).  The register cap this leaves (128
+// at 256 threads, 85 at 384) keeps the interpolators from spilling; measured
+// on the 2^24 cube, 256 threads suit trilinear, prism and pyramid and 384 the
+// tetrahedral method (512 threads, 64 registers, spilled: 11-21% slower).
+template <int METHOD>
+struct SmemThreads {
+    static constexpr int value = METHOD == MACT_TETRA ? 384 : 256;
+};
 
 // --------------------------------------------------------------- packing
 
@@ -359,13 +367,14 @@ template <int METHOD, int N, bool SMEM>
 static cudaError_t launch_sel(const mact_ctx &h, const ImageDesc &im, const float *lut, const float4 *lut4, int n,
                               int32_t *sel, cudaStream_t s)
 {
-    constexpr int T = SMEM ? kLutThreadsSmem : kThreads;
-    // register caps: 64 (2 x 512 threads) for the shared-memory LUT; 80
-    // (3 x 256 threads) for the global one, where the 64 cap spilled and
-    // measured 5-8% slower
+    constexpr int T = SMEM ? SmemThreads<METHOD>::value : kThreads;
+    // two CTAs per SM for the shared-memory LUT; three (80 registers) for the
+    // global one, where a 64-register cap spilled and measured 5-8% slower
     constexpr int MINB = SMEM ? 2 : 3;
-    if (sel) return launch_interp<T, MINB, METHOD, N, SMEM, true>(h, im, lut, lut4, n, sel, s);
-    return launch_interp<T, MINB, METHOD, N, SMEM, false>(h, im, lut, lut4, n, sel, s);
+    ImageDesc imt = im;   // one long row of tiles of this launch shape
+    imt.tiles_per_row = (im.width + TileShape<T>::px - 1) / TileShape<T>::px;
+    if (sel) return launch_interp<T, MINB, METHOD, N, SMEM, true>(h, imt, lut, lut4, n, sel, s);
+    return launch_interp<T, MINB, METHOD, N, SMEM, false>(h, imt, lut, lut4, n, sel, s);
 }
 
 template <int METHOD>
@@ -392,8 +401,6 @@ cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut,
     im.opitch = npix;
     im.space = MACT_CIELAB;
     im.dtype = MACT_F32;
-    const int P = n <= kLutSmemMaxN ? TileShape<kLutThreadsSmem>::px : TileShape<kThreads>::px;
-    im.tiles_per_row = (npix + P - 1) / P;
     switch (method) {
     case MACT_TRILINEAR: return interp_method<MACT_TRILINEAR>(h, im, d_lut, d_lut4, n, d_sel, s);
     case MACT_PRISM: return interp_method<MACT_PRISM>(h, im, d_lut, d_lut4, n, d_sel, s);
