@@ -35,6 +35,15 @@ struct SmemThreads {
     static constexpr int value = METHOD == MACT_TETRA ? 384 : 256;
 };
 
+// Launch shape of the global-memory LUT kernels (about 24 resident warps per
+// SM, 80 registers): trilinear 256 threads x 3 CTAs; the other methods
+// 128 x 6, which measured 2-6% faster for them and 4% slower for trilinear.
+template <int METHOD>
+struct GlobalShape {
+    static constexpr int threads = METHOD == MACT_TRILINEAR ? 256 : 128;
+    static constexpr int ctas = METHOD == MACT_TRILINEAR ? 3 : 6;
+};
+
 // --------------------------------------------------------------- packing
 
 __global__ void k_lut_build(int n, float *__restrict__ lut, mact_rgb_def d)
@@ -367,10 +376,10 @@ template <int METHOD, int N, bool SMEM>
 static cudaError_t launch_sel(const mact_ctx &h, const ImageDesc &im, const float *lut, const float4 *lut4, int n,
                               int32_t *sel, cudaStream_t s)
 {
-    constexpr int T = SMEM ? SmemThreads<METHOD>::value : kThreads;
-    // two CTAs per SM for the shared-memory LUT; three (80 registers) for the
-    // global one, where a 64-register cap spilled and measured 5-8% slower
-    constexpr int MINB = SMEM ? 2 : 3;
+    constexpr int T = SMEM ? SmemThreads<METHOD>::value : GlobalShape<METHOD>::threads;
+    // two CTAs per SM for the shared-memory LUT; for the global one a cap of
+    // 80 registers, where 64 spilled and measured 5-8% slower
+    constexpr int MINB = SMEM ? 2 : GlobalShape<METHOD>::ctas;
     ImageDesc imt = im;   // one long row of tiles of this launch shape
     imt.tiles_per_row = (im.width + TileShape<T>::px - 1) / TileShape<T>::px;
     if (sel) return launch_interp<T, MINB, METHOD, N, SMEM, true>(h, imt, lut, lut4, n, sel, s);
