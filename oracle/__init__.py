@@ -136,6 +136,27 @@ def cbrt_coeffs(n, m):
     return p, q
 
 
+_CBRT_FITS = {}
+
+
+def cbrt_minimax(n, m):
+    """(p, q, E) of the minimax rational p_n/q_m of t^(1/3) on [0.008856, 1]
+    (the interval of Figure fig_cbrt), from the oracle's own Remez exchange,
+    q(0) = 1: for the degrees Table tab_cbrt_rat does not print (and the
+    converged form of those it does)."""
+    if (n, m) not in _CBRT_FITS:
+        p, q, E, xs, es = remez.remez_rational(np.cbrt, n, m, 0.008856, 1.0)
+        _CBRT_FITS[(n, m)] = (list(p), list(q), E, xs, es)
+    p, q, E, _, _ = _CBRT_FITS[(n, m)]
+    return p, q, E
+
+
+def cbrt_minimax_extrema(n, m):
+    """The reference points and signed errors of cbrt_minimax(n, m)."""
+    cbrt_minimax(n, m)
+    return _CBRT_FITS[(n, m)][3], _CBRT_FITS[(n, m)][4]
+
+
 def hsi_coeffs(n, printed=False):
     """Coefficients replacing arctan(sqrt(3) x): the oracle's own Remez fit on
     [0, 1] (default) or Table tab_arctan as printed (n=2 sign read as minus)."""
@@ -294,30 +315,32 @@ def cube_eps_lut(method, lut, rgbdef=None):
 
 # --------------------------------------------- differentiable RGB -> CIELAB
 
-def _lab_args(exact, n, m):
-    p, q = cbrt_coeffs(n, m)
+def _lab_args(exact, n, m, p=None, q=None):
+    if p is None:
+        p, q = cbrt_coeffs(n, m)
     return (0 if exact else 1), _darr(p), len(p) - 1, _darr(q or [1.0]), ((len(q) - 1) if q is not None else -1)
 
 
-def lab_linear(x, exact=False, n=4, m=4, rgbdef=None):
-    """CIELAB of LINEAR RGB x, shape (N, 3, ...) -> same shape (FP64)."""
+def lab_linear(x, exact=False, n=4, m=4, rgbdef=None, p=None, q=None):
+    """CIELAB of LINEAR RGB x, shape (N, 3, ...) -> same shape (FP64).  p, q:
+    explicit cube-root coefficients (default: Table tab_cbrt_rat (n, m))."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     nb, hw = x.shape[0], x[0, 0].size
     out = np.empty_like(x)
     d = rgbdef or bt709_d65()
-    mode, pa, pn, qa, qm = _lab_args(exact, n, m)
+    mode, pa, pn, qa, qm = _lab_args(exact, n, m, p, q)
     lib().orc_lab_linear(ctypes.byref(d), mode, pa, pn, qa, qm, _ptr(x, _D), nb, hw, _ptr(out, _D))
     return out
 
 
-def lab_loss_grad(x, target, exact=False, n=4, m=4, rgbdef=None, grad=True):
+def lab_loss_grad(x, target, exact=False, n=4, m=4, rgbdef=None, grad=True, p=None, q=None):
     """(mean Delta E*ab of lab_linear(x) vs target, analytic dLoss/dx)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     t = np.ascontiguousarray(target, dtype=np.float64)
     nb, hw = x.shape[0], x[0, 0].size
     g = np.empty_like(x) if grad else None
     d = rgbdef or bt709_d65()
-    mode, pa, pn, qa, qm = _lab_args(exact, n, m)
+    mode, pa, pn, qa, qm = _lab_args(exact, n, m, p, q)
     loss = lib().orc_lab_loss_grad(ctypes.byref(d), mode, pa, pn, qa, qm, _ptr(x, _D), _ptr(t, _D), nb, hw,
                                    _ptr(g, _D) if grad else None)
     return loss, g

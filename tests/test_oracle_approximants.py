@@ -134,3 +134,47 @@ def test_hsi_printed_n2_sign():
     assert abs(np.arctan(SQ3 * x) - remez.poly_eval(bad, x))[0] > 1.0
     cc, E, _, _ = remez.remez_poly(lambda x: np.arctan(SQ3 * x), 2, *T.HSI_PRINTED_INTERVAL)
     assert cc[2] == pytest.approx(good[2], rel=1e-4)
+
+
+# ---- cube-root rationals beyond the printed degrees ----------------------
+
+import oracle as O  # noqa: E402
+
+
+@pytest.mark.parametrize("n,m", [(4, 4), (5, 5), (6, 6), (5, 6)])
+def test_fitted_cube_root_rational_is_minimax(n, m):
+    """The oracle's Remez fit of t^(1/3) on [0.008856, 1] (the interval of
+    Figure fig_cbrt): by Chebyshev's alternation theorem the minimax rational
+    has n+m+2 error extrema of alternating sign and equal modulus; a dense
+    log-spaced grid, independent of the exchange's own, finds nothing above
+    that level, and the denominator has no zero on the interval."""
+    p, q, E = O.cbrt_minimax(n, m)
+    xs, es = O.cbrt_minimax_extrema(n, m)
+    es = np.asarray(es)
+    assert len(xs) == n + m + 2
+    assert np.all(np.sign(es[1:]) == -np.sign(es[:-1]))
+    assert np.max(np.abs(es)) - np.min(np.abs(es)) <= 1e-4 * E
+    t = np.geomspace(0.008856, 1.0, 400001)
+    den = np.polyval(np.asarray(q)[::-1], t)
+    assert np.all(den > 0)
+    err = np.cbrt(t) - np.polyval(np.asarray(p)[::-1], t) / den
+    assert np.max(np.abs(err)) <= E * (1 + 1e-4)
+
+
+def test_fitted_errors_fall_with_degree_and_beat_the_printed_row():
+    """Each added degree lowers the minimax error, and the converged (4,4)
+    lies below the printed (4,4) row's error (an unconverged fit)."""
+    eps44_printed = T.CBRT_RAT[(4, 4)][0]
+    E = {d: O.cbrt_minimax(*d)[2] for d in [(4, 4), (5, 5), (6, 6)]}
+    assert E[(6, 6)] < E[(5, 5)] < E[(4, 4)] < eps44_printed
+
+
+def test_fitted_six_six_cube_error_below_1e4():
+    """Over every 24-bit colour the (6,6) fit's CIELAB error (Delta E*ab in
+    FP64 against the exact transform) stays below 1e-4: the approximant
+    matches the exact transform to the level of FP32 rounding."""
+    p, q, _ = O.cbrt_minimax(6, 6)
+    avg, mx = O.cube_eps_cielab(p=p, q=q)
+    assert mx < 1e-4 and avg < mx
+    p4, q4, _ = O.cbrt_minimax(4, 4)
+    assert O.cube_eps_cielab(p=p4, q=q4)[1] > 10 * mx
