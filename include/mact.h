@@ -100,7 +100,15 @@ typedef struct {
  *             as printed (n = 2 with a2 = -7.497879e-01).  Default 0.
  *  sct_n, sct_m, sct_r  degrees (4 or 5) of the arcsin, arccos and f/g
  *             polynomials (Tables tab_arcsin, tab_arccos, tab_f, tab_g).
- *             Default (5, 5, 5). */
+ *             Default (5, 5, 5).
+ *  lab_coeffs 0: the cube-root coefficients of the tables, as printed
+ *             (default).  1: the minimax rational p_n/q_m of t^(1/3) on
+ *             [0.008856, 1] (Figure fig_cbrt's interval) fitted by the
+ *             library's own Remez exchange at create time, for any
+ *             1 <= lab_n, lab_m <= 6 -- degrees the table does not print
+ *             (the paper has no counterpart beyond (4, 4)); MACT_E_UNSUPPORTED
+ *             if the exchange does not converge.  Evaluated like the printed
+ *             rationals (f = 1 + (p - q)/q in FP32). */
 typedef struct {
     mact_rgb_def rgb;
     int32_t exact;
@@ -108,6 +116,7 @@ typedef struct {
     int32_t hsi_n;
     int32_t hsi_coeffs;
     int32_t sct_n, sct_m, sct_r;
+    int32_t lab_coeffs;
 } mact_config;
 
 /* One image.  rgb: pointer (device, or host memory the device addresses) to

@@ -12,6 +12,7 @@
 namespace mact {
 
 bool hsi_unit_interval_fit(int n, double *coef6, double *err);
+bool cbrt_rational_fit(int n, int m, double *p7, double *q7, double *err);
 
 // ---- coefficient tables of the paper (ascending powers) -------------------
 
@@ -111,7 +112,28 @@ static mact_status build_coeffs(const mact_config &cfg, Coeffs &co)
         return inval("invalid gamma parameters");
 
     // cube root
-    if (cfg.lab_m == 0) {
+    if (cfg.lab_coeffs != 0 && cfg.lab_coeffs != 1) return inval("lab_coeffs must be 0 or 1");
+    co.lab_deg = 4;
+    if (cfg.lab_coeffs == 1) {
+        // the library's own minimax rational of t^(1/3) on [0.008856, 1]
+        if (cfg.lab_n < 1 || cfg.lab_n > 6 || cfg.lab_m < 1 || cfg.lab_m > 6)
+            return inval("lab_coeffs = 1 needs 1 <= lab_n, lab_m <= 6");
+        double p[7], q[7], e = 0.0;
+        if (!cbrt_rational_fit(cfg.lab_n, cfg.lab_m, p, q, &e)) {
+            set_error("Remez exchange for the cube-root rational did not converge");
+            return MACT_E_UNSUPPORTED;
+        }
+        for (int i = 0; i < 7; ++i) {
+            co.lab_d[i] = (float)(p[i] - q[i]);   // f = 1 + (p - q)/q
+            co.lab_q[i] = (float)q[i];
+        }
+        for (int i = 0; i < 6; ++i) {             // derivatives, for the backward
+            co.lab_dd[i] = (float)((i + 1) * (p[i + 1] - q[i + 1]));
+            co.lab_dq[i] = (float)((i + 1) * q[i + 1]);
+        }
+        co.lab_rational = 1;
+        co.lab_deg = (cfg.lab_n <= 4 && cfg.lab_m <= 4) ? 4 : 6;
+    } else if (cfg.lab_m == 0) {
         if (cfg.lab_n < 2 || cfg.lab_n > 5) return inval("lab_n must be 2..5 for the polynomial (lab_m = 0)");
         for (int i = 0; i < 6; ++i) {
             co.lab_d[i] = (float)kCbrtPoly[cfg.lab_n - 2][i];
@@ -272,6 +294,7 @@ void mact_config_default(mact_config *cfg)
     cfg->hsi_n = 5;
     cfg->hsi_coeffs = 0;
     cfg->sct_n = cfg->sct_m = cfg->sct_r = 5;
+    cfg->lab_coeffs = 0;
 }
 
 mact_status mact_create(const mact_config *cfg, mact_handle *out)

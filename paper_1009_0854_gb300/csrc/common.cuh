@@ -24,11 +24,12 @@ struct Coeffs {
     double m64[9];       // rgb_to_xyz / white in FP64 (polynomial cube-root path)
     double lab_p64[6];   // polynomial cube root in FP64, degree 5 (zero-padded)
     float m[9];          // rgb_to_xyz row c divided by white[c]
-    float lab_d[6];      // rational: p - q (degree 4); polynomial: p (degree 5)
-    float lab_q[5];      // rational: q (degree 4)
-    float lab_dd[4];     // rational: d' = (p - q)' (degree 3)
-    float lab_dq[4];     // rational: q' (degree 3)
+    float lab_d[8];      // rational: p - q (degree <= 6); polynomial: p (degree 5); zero-padded
+    float lab_q[8];      // rational: q (degree <= 6)
+    float lab_dd[7];     // rational: d' = (p - q)' (degree <= 5)
+    float lab_dq[7];     // rational: q' (degree <= 5)
     int32_t lab_rational;
+    int32_t lab_deg;     // Horner degree of the rational's chains: 4 (n, m <= 4) or 6
     float hsi[6];        // arctan(sqrt(3) x) on |x| <= 1, degree 5
     float sct_p[6];      // 2 arcsin(y/sqrt 2), y = sqrt(1 - B/L), degree 5
     float sct_q[6];      // arccos(x) on [0, 0.5], degree 5

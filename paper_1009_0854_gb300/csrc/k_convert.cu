@@ -74,9 +74,10 @@ static cudaError_t dispatch_space(const mact_ctx &h, const ImageDesc &im, cudaSt
     const bool rat = h.co.lab_rational != 0;
     switch (im.space) {
     case MACT_CIELAB:
-        if (exact) return launch_one<OpCielab<true, true>, OutT, kTable32>(h, im, s);
-        if (rat) return launch_one<OpCielab<false, true>, OutT, kTable32>(h, im, s);
-        return launch_one<OpCielab<false, false>, OutT, kTable64>(h, im, s);
+        if (exact) return launch_one<OpCielab<true, 4>, OutT, kTable32>(h, im, s);
+        if (rat && h.co.lab_deg == 6) return launch_one<OpCielab<false, 6>, OutT, kTable32>(h, im, s);
+        if (rat) return launch_one<OpCielab<false, 4>, OutT, kTable32>(h, im, s);
+        return launch_one<OpCielab<false, 0>, OutT, kTable64>(h, im, s);
     case MACT_HSI:
         if (exact) return launch_one<WithTable<OpHsi<true>>, OutT, kNoTable>(h, im, s);
         return launch_one<WithTable<OpHsi<false>>, OutT, kNoTable>(h, im, s);
@@ -94,13 +95,13 @@ cudaError_t launch_convert(const mact_ctx &h, const ImageDesc &im, cudaStream_t 
 
 // ------------------------------------------------------------ batched form
 
-template <typename OutT, bool EXACT, bool RAT, int THREADS, int SUBS>
+template <typename OutT, bool EXACT, int RDEG, int THREADS, int SUBS>
 __device__ __forceinline__ void batch_tile(const ImageDesc &im, int64_t t, const float *sgam,
                                            const Coeffs &co, uint4 *sbuf)
 {
     float *scr = reinterpret_cast<float *>(sbuf + TileShape<THREADS, SUBS>::vecs);
     if (im.space == MACT_CIELAB) {
-        const OpCielab<EXACT, RAT> op{sgam, co};
+        const OpCielab<EXACT, RDEG> op{sgam, co};
         process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr, scr);
     } else if (im.space == MACT_HSI) {
         const OpHsi<EXACT> op{co};
@@ -111,7 +112,7 @@ __device__ __forceinline__ void batch_tile(const ImageDesc &im, int64_t t, const
     }
 }
 
-template <bool EXACT, bool RAT, int THREADS, int SUBS>
+template <bool EXACT, int RDEG, int THREADS, int SUBS>
 __global__ void __launch_bounds__(THREADS)
 k_batch(const ImageDesc *__restrict__ imgs, int32_t count, int64_t total,
         unsigned long long *__restrict__ ctr, const __grid_constant__ Coeffs co,
@@ -121,7 +122,7 @@ k_batch(const ImageDesc *__restrict__ imgs, int32_t count, int64_t total,
     __shared__ uint4 sbuf[TileShape<THREADS, SUBS>::vecs + TileShape<THREADS, SUBS>::scratch];
     __shared__ long long s_tile;
     __shared__ int s_img;
-    load_table((!EXACT && !RAT) ? kTable64 : kTable32, gamma, sgam64);
+    load_table((!EXACT && RDEG == 0) ? kTable64 : kTable32, gamma, sgam64);
     const float *sgam = reinterpret_cast<const float *>(sgam64);
     for (;;) {
         __syncthreads();   // previous tile finished with sbuf / s_tile
@@ -143,8 +144,8 @@ k_batch(const ImageDesc *__restrict__ imgs, int32_t count, int64_t total,
         if (t >= total) break;
         const ImageDesc &im = imgs[s_img];
         const int64_t lt = t - im.tile_begin;
-        if (im.dtype == MACT_F16) batch_tile<__half, EXACT, RAT, THREADS, SUBS>(im, lt, sgam, co, sbuf);
-        else batch_tile<float, EXACT, RAT, THREADS, SUBS>(im, lt, sgam, co, sbuf);
+        if (im.dtype == MACT_F16) batch_tile<__half, EXACT, RDEG, THREADS, SUBS>(im, lt, sgam, co, sbuf);
+        else batch_tile<float, EXACT, RDEG, THREADS, SUBS>(im, lt, sgam, co, sbuf);
     }
     // the last CTA out resets the counters for the next launch on the list
     if (threadIdx.x == 0) {
@@ -161,14 +162,14 @@ k_batch(const ImageDesc *__restrict__ imgs, int32_t count, int64_t total,
 // the kernel's parameter block instead of device memory: the launch needs no
 // copy and no device counter.  Tiles are uniform (all full but each image's
 // last), so CTAs take them grid-stride, t = blockIdx.x + k * gridDim.x.
-template <bool EXACT, bool RAT, int THREADS, int SUBS>
+template <bool EXACT, int RDEG, int THREADS, int SUBS>
 __global__ void __launch_bounds__(THREADS)
 k_batch_param(const __grid_constant__ ParamList list, int32_t count, int64_t total,
               const __grid_constant__ Coeffs co, const float *__restrict__ gamma)
 {
     __shared__ double sgam64[256];
     __shared__ uint4 sbuf[TileShape<THREADS, SUBS>::vecs + TileShape<THREADS, SUBS>::scratch];
-    load_table((!EXACT && !RAT) ? kTable64 : kTable32, gamma, sgam64);
+    load_table((!EXACT && RDEG == 0) ? kTable64 : kTable32, gamma, sgam64);
     const float *sgam = reinterpret_cast<const float *>(sgam64);
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
         __syncthreads();   // previous tile finished with sbuf
@@ -180,8 +181,8 @@ k_batch_param(const __grid_constant__ ParamList list, int32_t count, int64_t tot
         }
         const ImageDesc &im = list.img[lo];
         const int64_t lt = t - im.tile_begin;
-        if (im.dtype == MACT_F16) batch_tile<__half, EXACT, RAT, THREADS, SUBS>(im, lt, sgam, co, sbuf);
-        else batch_tile<float, EXACT, RAT, THREADS, SUBS>(im, lt, sgam, co, sbuf);
+        if (im.dtype == MACT_F16) batch_tile<__half, EXACT, RDEG, THREADS, SUBS>(im, lt, sgam, co, sbuf);
+        else batch_tile<float, EXACT, RDEG, THREADS, SUBS>(im, lt, sgam, co, sbuf);
     }
 }
 
@@ -197,15 +198,15 @@ bool batch_cfg_supported(const BatchCfg &cfg)
     return false;
 }
 
-template <bool EXACT, bool RAT, int THREADS, int SUBS>
+template <bool EXACT, int RDEG, int THREADS, int SUBS>
 static int occ_batch()
 {
     static const int occ = [] {   // thread-safe one-time init
         int o = 0, op = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch<EXACT, RAT, THREADS, SUBS>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch<EXACT, RDEG, THREADS, SUBS>,
                                                                       THREADS, 0);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_batch_param<EXACT, RAT, THREADS, SUBS>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_batch_param<EXACT, RDEG, THREADS, SUBS>,
                                                               THREADS, 0);
         if (op < o) o = op;   // one figure serves both forms
         return (e != cudaSuccess || o <= 0) ? 1 : o;
@@ -213,10 +214,10 @@ static int occ_batch()
     return occ;
 }
 
-template <bool EXACT, bool RAT>
+template <bool EXACT, int RDEG>
 static int occ_shape(const BatchCfg &cfg)
 {
-#define MACT_OCC(T, S) if (cfg.threads == T && cfg.subs == S) return occ_batch<EXACT, RAT, T, S>();
+#define MACT_OCC(T, S) if (cfg.threads == T && cfg.subs == S) return occ_batch<EXACT, RDEG, T, S>();
     MACT_BATCH_SHAPES(MACT_OCC)
 #undef MACT_OCC
     return 1;
@@ -224,17 +225,18 @@ static int occ_shape(const BatchCfg &cfg)
 
 int batch_blocks_per_sm(const mact_ctx &h, const BatchCfg &cfg)
 {
-    if (h.cfg.exact) return occ_shape<true, true>(cfg);
-    return h.co.lab_rational ? occ_shape<false, true>(cfg) : occ_shape<false, false>(cfg);
+    if (h.cfg.exact) return occ_shape<true, 4>(cfg);
+    if (!h.co.lab_rational) return occ_shape<false, 0>(cfg);
+    return h.co.lab_deg == 6 ? occ_shape<false, 6>(cfg) : occ_shape<false, 4>(cfg);
 }
 
-template <bool EXACT, bool RAT>
+template <bool EXACT, int RDEG>
 static cudaError_t launch_shape(const mact_ctx &h, const ImageDesc *d_imgs, int32_t count, int64_t total,
                                 unsigned long long *d_ctr, int grid, cudaStream_t s, const BatchCfg &cfg)
 {
 #define MACT_LAUNCH(T, S)                                                                               \
     if (cfg.threads == T && cfg.subs == S) {                                                            \
-        k_batch<EXACT, RAT, T, S><<<grid, T, 0, s>>>(d_imgs, count, total, d_ctr, h.co, h.d_gamma);     \
+        k_batch<EXACT, RDEG, T, S><<<grid, T, 0, s>>>(d_imgs, count, total, d_ctr, h.co, h.d_gamma);     \
         return cudaGetLastError();                                                                      \
     }
     MACT_BATCH_SHAPES(MACT_LAUNCH)
@@ -242,13 +244,13 @@ static cudaError_t launch_shape(const mact_ctx &h, const ImageDesc *d_imgs, int3
     return cudaErrorInvalidValue;
 }
 
-template <bool EXACT, bool RAT>
+template <bool EXACT, int RDEG>
 static cudaError_t launch_shape_param(const mact_ctx &h, const ParamList &list, int32_t count, int64_t total,
                                       int grid, cudaStream_t s, const BatchCfg &cfg)
 {
 #define MACT_LAUNCH(T, S)                                                                               \
     if (cfg.threads == T && cfg.subs == S) {                                                            \
-        k_batch_param<EXACT, RAT, T, S><<<grid, T, 0, s>>>(list, count, total, h.co, h.d_gamma);        \
+        k_batch_param<EXACT, RDEG, T, S><<<grid, T, 0, s>>>(list, count, total, h.co, h.d_gamma);        \
         return cudaGetLastError();                                                                      \
     }
     MACT_BATCH_SHAPES(MACT_LAUNCH)
@@ -260,17 +262,19 @@ cudaError_t launch_batch_param(const mact_ctx &h, const ParamList &list, int32_t
                                cudaStream_t s, const BatchCfg &cfg)
 {
     if (count < 1 || count > kParamImages) return cudaErrorInvalidValue;
-    if (h.cfg.exact) return launch_shape_param<true, true>(h, list, count, total, grid, s, cfg);
-    if (h.co.lab_rational) return launch_shape_param<false, true>(h, list, count, total, grid, s, cfg);
-    return launch_shape_param<false, false>(h, list, count, total, grid, s, cfg);
+    if (h.cfg.exact) return launch_shape_param<true, 4>(h, list, count, total, grid, s, cfg);
+    if (!h.co.lab_rational) return launch_shape_param<false, 0>(h, list, count, total, grid, s, cfg);
+    if (h.co.lab_deg == 6) return launch_shape_param<false, 6>(h, list, count, total, grid, s, cfg);
+    return launch_shape_param<false, 4>(h, list, count, total, grid, s, cfg);
 }
 
 cudaError_t launch_batch(const mact_ctx &h, const ImageDesc *d_imgs, int32_t count, int64_t total,
                          unsigned long long *d_ctr, int grid, cudaStream_t s, const BatchCfg &cfg)
 {
-    if (h.cfg.exact) return launch_shape<true, true>(h, d_imgs, count, total, d_ctr, grid, s, cfg);
-    if (h.co.lab_rational) return launch_shape<false, true>(h, d_imgs, count, total, d_ctr, grid, s, cfg);
-    return launch_shape<false, false>(h, d_imgs, count, total, d_ctr, grid, s, cfg);
+    if (h.cfg.exact) return launch_shape<true, 4>(h, d_imgs, count, total, d_ctr, grid, s, cfg);
+    if (!h.co.lab_rational) return launch_shape<false, 0>(h, d_imgs, count, total, d_ctr, grid, s, cfg);
+    if (h.co.lab_deg == 6) return launch_shape<false, 6>(h, d_imgs, count, total, d_ctr, grid, s, cfg);
+    return launch_shape<false, 4>(h, d_imgs, count, total, d_ctr, grid, s, cfg);
 }
 
 }  // namespace mact

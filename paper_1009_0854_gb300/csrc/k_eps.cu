@@ -108,7 +108,7 @@ __device__ __forceinline__ void eps_body(const Op &op, const Exact64 &x, double2
     if (threadIdx.x == 0) partial[blockIdx.x] = make_double2(rs[0], rm[0]);
 }
 
-template <int KIND, bool EXACT, bool RAT>
+template <int KIND, bool EXACT, int RDEG>
 __global__ void __launch_bounds__(kEpsThreads)
 k_eps_space(const __grid_constant__ Coeffs co, const float *__restrict__ gamma, Exact64 x, double2 *partial)
 {
@@ -116,7 +116,7 @@ k_eps_space(const __grid_constant__ Coeffs co, const float *__restrict__ gamma, 
     for (int i = threadIdx.x; i < 256; i += blockDim.x) sgam[i] = gamma[i];
     __syncthreads();
     if (KIND == 0) {
-        const OpCielab<EXACT, RAT> op{RAT || EXACT ? sgam : reinterpret_cast<const float *>(x.g64), co};
+        const OpCielab<EXACT, RDEG> op{RDEG != 0 || EXACT ? sgam : reinterpret_cast<const float *>(x.g64), co};
         eps_body<0>(op, x, partial);
     } else if (KIND == 1) {
         const OpHsi<EXACT> op{co};
@@ -255,9 +255,15 @@ static Exact64 exact_of(const mact_ctx &h, const double *d_m64)
 template <int KIND>
 static void launch_space(const mact_ctx &h, int grid, const Exact64 &x, double2 *partial, cudaStream_t s)
 {
-    if (h.cfg.exact) k_eps_space<KIND, true, true><<<grid, kEpsThreads, 0, s>>>(h.co, h.d_gamma, x, partial);
-    else if (h.co.lab_rational) k_eps_space<KIND, false, true><<<grid, kEpsThreads, 0, s>>>(h.co, h.d_gamma, x, partial);
-    else k_eps_space<KIND, false, false><<<grid, kEpsThreads, 0, s>>>(h.co, h.d_gamma, x, partial);
+    if (h.cfg.exact) {
+        k_eps_space<KIND, true, 4><<<grid, kEpsThreads, 0, s>>>(h.co, h.d_gamma, x, partial);
+    } else if constexpr (KIND != 0) {   // the cube-root form matters to CIELAB only
+        k_eps_space<KIND, false, 4><<<grid, kEpsThreads, 0, s>>>(h.co, h.d_gamma, x, partial);
+    } else {
+        if (!h.co.lab_rational) k_eps_space<0, false, 0><<<grid, kEpsThreads, 0, s>>>(h.co, h.d_gamma, x, partial);
+        else if (h.co.lab_deg == 6) k_eps_space<0, false, 6><<<grid, kEpsThreads, 0, s>>>(h.co, h.d_gamma, x, partial);
+        else k_eps_space<0, false, 4><<<grid, kEpsThreads, 0, s>>>(h.co, h.d_gamma, x, partial);
+    }
 }
 
 // target: 0..2 = space of the handle's transform; 3 = LUT (method, d_lut4, n)

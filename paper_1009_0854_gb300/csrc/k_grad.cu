@@ -23,7 +23,9 @@ namespace mact {
 
 constexpr int kGradThreads = 256;
 
-template <bool EXACT>
+// FORM: 0 = the exact cube root; 4 or 6 = the rational with chains of that
+// degree (derivative chains one lower).
+template <int FORM>
 __device__ __forceinline__ void f_df(float t, const Coeffs &co, float &f, float &df)
 {
     if (t <= kKnee) {
@@ -31,16 +33,17 @@ __device__ __forceinline__ void f_df(float t, const Coeffs &co, float &f, float 
         df = kLinSlope;
         return;
     }
-    if (EXACT) {
+    if (FORM == 0) {
         f = cbrtf(t);
         df = f * rcp_nr(3.0f * t);
     } else {
-        const float d = horner<4>(co.lab_d, t);
-        const float q = horner<4>(co.lab_q, t);
+        constexpr int D = FORM == 0 ? 4 : FORM;
+        const float d = horner<D>(co.lab_d, t);
+        const float q = horner<D>(co.lab_q, t);
         const float r = rcp_nr(q);
         f = fmaf(d, r, 1.0f);
-        const float dd = horner<3>(co.lab_dd, t);
-        const float dq = horner<3>(co.lab_dq, t);
+        const float dd = horner<D - 1>(co.lab_dd, t);
+        const float dq = horner<D - 1>(co.lab_dq, t);
         df = fmaf(dd, q, -d * dq) * (r * r);
     }
 }
@@ -50,7 +53,7 @@ struct PixelLab {
     float df[3];
 };
 
-template <bool EXACT>
+template <int FORM>
 __device__ __forceinline__ PixelLab lab_of(float x0, float x1, float x2, const Coeffs &co)
 {
     PixelLab p;
@@ -58,7 +61,7 @@ __device__ __forceinline__ PixelLab lab_of(float x0, float x1, float x2, const C
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float t = fmaf(co.m[3 * c + 2], x2, fmaf(co.m[3 * c + 1], x1, co.m[3 * c] * x0));
-        f_df<EXACT>(t, co, f[c], p.df[c]);
+        f_df<FORM>(t, co, f[c], p.df[c]);
     }
     p.lab[0] = fmaf(116.0f, f[1], -16.0f);
     p.lab[1] = 500.0f * (f[0] - f[1]);
@@ -114,7 +117,7 @@ __device__ __forceinline__ void store_item(float *p, int64_t o, const float (&v)
     else __stcs(p + o, v[0]);
 }
 
-template <bool EXACT, bool VEC>
+template <int FORM, bool VEC>
 __global__ void __launch_bounds__(kGradThreads)
 k_lab_forward(const float *__restrict__ x, Geometry g, float *__restrict__ lab, const __grid_constant__ Coeffs co)
 {
@@ -127,7 +130,7 @@ k_lab_forward(const float *__restrict__ x, Geometry g, float *__restrict__ lab, 
         load_item<VEC>(x, o + 2 * g.hw, x2);
 #pragma unroll
         for (int j = 0; j < W; ++j) {
-            const PixelLab p = lab_of<EXACT>(x0[j], x1[j], x2[j], co);
+            const PixelLab p = lab_of<FORM>(x0[j], x1[j], x2[j], co);
             l0[j] = p.lab[0]; l1[j] = p.lab[1]; l2[j] = p.lab[2];
         }
         store_item<VEC>(lab, o, l0);
@@ -136,7 +139,7 @@ k_lab_forward(const float *__restrict__ x, Geometry g, float *__restrict__ lab, 
     }
 }
 
-template <bool EXACT, bool VEC>
+template <int FORM, bool VEC>
 __global__ void __launch_bounds__(kGradThreads)
 k_lab_backward(const float *__restrict__ x, const float *__restrict__ glab, Geometry g, float *__restrict__ gx,
                const __grid_constant__ Coeffs co)
@@ -153,7 +156,7 @@ k_lab_backward(const float *__restrict__ x, const float *__restrict__ glab, Geom
         load_item<VEC>(glab, o + 2 * g.hw, a2);
 #pragma unroll
         for (int j = 0; j < W; ++j) {
-            const PixelLab p = lab_of<EXACT>(x0[j], x1[j], x2[j], co);
+            const PixelLab p = lab_of<FORM>(x0[j], x1[j], x2[j], co);
             back(p, a0[j], a1[j], a2[j], co, x0[j], x1[j], x2[j]);
         }
         store_item<VEC>(gx, o, x0);
@@ -162,7 +165,7 @@ k_lab_backward(const float *__restrict__ x, const float *__restrict__ glab, Geom
     }
 }
 
-template <bool EXACT, bool GRAD, bool VEC>
+template <int FORM, bool GRAD, bool VEC>
 __global__ void __launch_bounds__(kGradThreads)
 k_lab_delta_e(const float *__restrict__ x, const float *__restrict__ tgt, Geometry g, float inv_npix,
               float *__restrict__ gx, double *__restrict__ partial, const __grid_constant__ Coeffs co)
@@ -181,7 +184,7 @@ k_lab_delta_e(const float *__restrict__ x, const float *__restrict__ tgt, Geomet
         float sum = 0.0f;
 #pragma unroll
         for (int j = 0; j < W; ++j) {
-            const PixelLab p = lab_of<EXACT>(x0[j], x1[j], x2[j], co);
+            const PixelLab p = lab_of<FORM>(x0[j], x1[j], x2[j], co);
             const float dl = p.lab[0] - t0[j], da = p.lab[1] - t1[j], db = p.lab[2] - t2[j];
             const float de = sqrtf(fmaf(dl, dl, fmaf(da, da, db * db)));
             sum += de;
@@ -249,17 +252,27 @@ static bool use_vec(int64_t hw, std::initializer_list<const void *> ptrs)
     return true;
 }
 
+// 0: exact cube root; 4 or 6: the rational's chain degree (the polynomial
+// cube root is refused by the entry points before launch)
+static int grad_form(const mact_ctx &h) { return h.cfg.exact ? 0 : h.co.lab_deg; }
+
 cudaError_t launch_lab_forward(const mact_ctx &h, const float *x, int64_t nb, int64_t hw, float *lab, cudaStream_t s)
 {
     const bool v = use_vec(hw, {x, lab});
     const Geometry g = geometry(nb, hw, v);
     const int grid = grad_grid(h, g.items);
-    if (h.cfg.exact) {
-        if (v) k_lab_forward<true, true><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
-        else k_lab_forward<true, false><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
-    } else {
-        if (v) k_lab_forward<false, true><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
-        else k_lab_forward<false, false><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
+    switch (grad_form(h)) {
+    case 0:
+        if (v) k_lab_forward<0, true><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
+        else k_lab_forward<0, false><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
+        break;
+    case 6:
+        if (v) k_lab_forward<6, true><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
+        else k_lab_forward<6, false><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
+        break;
+    default:
+        if (v) k_lab_forward<4, true><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
+        else k_lab_forward<4, false><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
     }
     return cudaGetLastError();
 }
@@ -270,24 +283,30 @@ cudaError_t launch_lab_backward(const mact_ctx &h, const float *x, const float *
     const bool v = use_vec(hw, {x, glab, gx});
     const Geometry g = geometry(nb, hw, v);
     const int grid = grad_grid(h, g.items);
-    if (h.cfg.exact) {
-        if (v) k_lab_backward<true, true><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
-        else k_lab_backward<true, false><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
-    } else {
-        if (v) k_lab_backward<false, true><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
-        else k_lab_backward<false, false><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
+    switch (grad_form(h)) {
+    case 0:
+        if (v) k_lab_backward<0, true><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
+        else k_lab_backward<0, false><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
+        break;
+    case 6:
+        if (v) k_lab_backward<6, true><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
+        else k_lab_backward<6, false><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
+        break;
+    default:
+        if (v) k_lab_backward<4, true><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
+        else k_lab_backward<4, false><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
     }
     return cudaGetLastError();
 }
 
-template <bool EXACT>
+template <int FORM>
 static void delta_e_launch(bool grad, bool v, int grid, cudaStream_t s, const float *x, const float *tgt,
                            const Geometry &g, float inv, float *gx, double *partial, const Coeffs &co)
 {
-    if (grad && v) k_lab_delta_e<EXACT, true, true><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co);
-    else if (grad) k_lab_delta_e<EXACT, true, false><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co);
-    else if (v) k_lab_delta_e<EXACT, false, true><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co);
-    else k_lab_delta_e<EXACT, false, false><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co);
+    if (grad && v) k_lab_delta_e<FORM, true, true><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co);
+    else if (grad) k_lab_delta_e<FORM, true, false><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co);
+    else if (v) k_lab_delta_e<FORM, false, true><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co);
+    else k_lab_delta_e<FORM, false, false><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co);
 }
 
 cudaError_t launch_lab_delta_e(const mact_ctx &h, const float *x, const float *tgt, int64_t nb, int64_t hw,
@@ -298,8 +317,11 @@ cudaError_t launch_lab_delta_e(const mact_ctx &h, const float *x, const float *t
     const Geometry g = geometry(nb, hw, v);
     const int grid = grad_grid(h, g.items);
     const float inv = (float)(1.0 / (double)(nb * hw));
-    if (h.cfg.exact) delta_e_launch<true>(gx != nullptr, v, grid, s, x, tgt, g, inv, gx, partial, h.co);
-    else delta_e_launch<false>(gx != nullptr, v, grid, s, x, tgt, g, inv, gx, partial, h.co);
+    switch (grad_form(h)) {
+    case 0: delta_e_launch<0>(gx != nullptr, v, grid, s, x, tgt, g, inv, gx, partial, h.co); break;
+    case 6: delta_e_launch<6>(gx != nullptr, v, grid, s, x, tgt, g, inv, gx, partial, h.co); break;
+    default: delta_e_launch<4>(gx != nullptr, v, grid, s, x, tgt, g, inv, gx, partial, h.co);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sum_partials<<<1, kGradThreads, 0, s>>>(partial, grid, 1.0 / (double)(nb * hw), loss);

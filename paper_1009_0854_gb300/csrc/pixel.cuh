@@ -27,10 +27,13 @@ constexpr float kLinOffset = 16.0f / 116.0f;
 // absolute errors by 500 and 200, d is small and its rounding error scales
 // with it, so the worst a* error over the 2^24 colours drops from ~2.2e-4
 // (p/q) to ~1.2e-4.
+// DEG: Horner degree of both chains (4 for the printed rationals, 6 for the
+// library's fits up to (6, 6); higher coefficients are zero).
+template <int DEG>
 __device__ __forceinline__ float f_mact(float t, const Coeffs &co)
 {
-    float d = horner<4>(co.lab_d, t);
-    float q = horner<4>(co.lab_q, t);
+    float d = horner<DEG>(co.lab_d, t);
+    float q = horner<DEG>(co.lab_q, t);
     float fa = fmaf(d, rcp_nr(q), 1.0f);
     float fl = fmaf(kLinSlope, t, kLinOffset);
     return t > kKnee ? fa : fl;
@@ -55,14 +58,16 @@ __device__ __forceinline__ float f_exact(float t)
     return t > kKnee ? cbrtf(t) : fl;
 }
 
-template <bool EXACT, bool RATIONAL>
+// RDEG: 0 = the FP64 cube-root polynomial; 4 or 6 = the rational with
+// chains of that degree (ignored when EXACT).
+template <bool EXACT, int RDEG>
 struct OpCielab {
     const float *gam;   // 256-entry linearisation table in shared memory
     const Coeffs &co;
     __device__ __forceinline__ int operator()(uint32_t r, uint32_t g, uint32_t b, float &o0, float &o1,
                                               float &o2) const
     {
-        if (!EXACT && !RATIONAL) {
+        if (!EXACT && RDEG == 0) {
             const double *g64 = reinterpret_cast<const double *>(gam);
             const double k0 = g64[r], k1 = g64[g], k2 = g64[b];
             const double *m = co.m64;
@@ -82,7 +87,8 @@ struct OpCielab {
         if (EXACT) {
             fx = f_exact(tx); fy = f_exact(ty); fz = f_exact(tz);
         } else {
-            fx = f_mact(tx, co); fy = f_mact(ty, co); fz = f_mact(tz, co);
+            constexpr int D = RDEG == 0 ? 4 : RDEG;   // (RDEG 0 returned above)
+            fx = f_mact<D>(tx, co); fy = f_mact<D>(ty, co); fz = f_mact<D>(tz, co);
         }
         o0 = fmaf(116.0f, fy, -16.0f);
         o1 = 500.0f * (fx - fy);

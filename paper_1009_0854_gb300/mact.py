@@ -44,7 +44,8 @@ class RGBDef(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("rgb", RGBDef), ("exact", ctypes.c_int32), ("lab_n", ctypes.c_int32),
                 ("lab_m", ctypes.c_int32), ("hsi_n", ctypes.c_int32), ("hsi_coeffs", ctypes.c_int32),
-                ("sct_n", ctypes.c_int32), ("sct_m", ctypes.c_int32), ("sct_r", ctypes.c_int32)]
+                ("sct_n", ctypes.c_int32), ("sct_m", ctypes.c_int32), ("sct_r", ctypes.c_int32),
+                ("lab_coeffs", ctypes.c_int32)]
 
 
 class Image(ctypes.Structure):
