@@ -402,14 +402,15 @@ def run_large_workload(args):
     dev = torch.device("cuda", 0)
     hbm, _ = peaks()
     hm, he = mact.mact_create(), mact.mact_create(exact=1)
+    h66 = mact.mact_create(lab_coeffs=1, lab_n=6, lab_m=6)   # fitted (6,6) cube root
     rows = {}
     for side in (8192, 16384):
         rgb = torch.from_numpy(synth.gradient_noise_image(side, side, seed=0)).to(dev)
         npx = side * side
         for dt, dname, bpp in ((torch.float32, "f32", 15), (torch.float16, "f16", 9)):
             out = torch.empty((3, side, side), dtype=dt, device=dev)
-            for hname, h in (("mact", hm), ("exact", he)):
-                for space in ("cielab", "hsi", "sct"):
+            for hname, h in (("mact", hm), ("exact", he), ("mact66", h66)):
+                for space in (("cielab",) if hname == "mact66" else ("cielab", "hsi", "sct")):
                     fn = lambda: mact.mact_convert(h, rgb, space, out=out)      # noqa: E731
                     for _ in range(3):
                         fn()
@@ -429,7 +430,8 @@ def run_large_workload(args):
         del rgb
         torch.cuda.empty_cache()
     print(json.dumps({"workload": "large: 8192^2 and 16384^2 single images (gradients + noise), %d B/px FP32, "
-                      "%d B/px FP16, peak %.1f GB/s measured" % (15, 9, hbm), "rows": rows}))
+                      "%d B/px FP16, peak %.1f GB/s measured; mact66 = the library's fitted (6,6) cube-root "
+                      "rational" % (15, 9, hbm), "rows": rows}))
 
 
 def run_batch_workload(args):
@@ -613,8 +615,10 @@ def run_serve_workload(args):
     pinned host input and output (outputs carved from one pinned ring shared by
     every path), through the continuous-batching server (MACT, 16 GB staging
     budget) in direct mode (the kernel reads and writes the pinned buffers in
-    place) and in staged mode (copies through the arena), and through the
-    plain path (one request at a time: H2D, exact-libm kernel, D2H).  Every
+    place) and in staged mode (copies through the arena), in direct mode with
+    the library's fitted (6,6) cube-root rational (max Delta E near the exact
+    path's), and through the plain path (one request at a time: H2D,
+    exact-libm kernel, D2H).  Every
     path first serves an untimed 0.25 s warm-up trace.  Latency counts from
     the trace's arrival time."""
     import torch
@@ -658,10 +662,12 @@ def run_serve_workload(args):
 
     h = mact.mact_create()
 
-    def served(tr, mode):
+    h66 = mact.mact_create(lab_coeffs=1, lab_n=6, lab_m=6)
+
+    def served(tr, mode, hs=None):
         """The driver submits at each arrival time and, while waiting for the
         next one, retires every finished request (its ring slot is released)."""
-        srv = mact.mact_serve_create(h, 16 << 30, max_slots=128)
+        srv = mact.mact_serve_create(hs or h, 16 << 30, max_slots=128)
         mact.mact_serve_set_mode(srv, mode)
         inflight = collections.OrderedDict()    # ticket -> (arrival, submit, ring entry)
         lat = []
@@ -758,6 +764,7 @@ def run_serve_workload(args):
 
     served(warm_trace, "direct")
     served(warm_trace, "staged")
+    served(warm_trace, "direct", h66)
     plain(warm_trace)
 
     def same_delta_e():
@@ -778,12 +785,16 @@ def run_serve_workload(args):
             k += 1
         srv.close()
         e_mact = mact.mact_cube_error(h, "cielab")
+        e_66 = mact.mact_cube_error(h66, "cielab")
         e_exact = mact.mact_cube_error(mact.mact_create(exact=1), "cielab")
         return {"sampled_requests": k, "served_bit_identical_to_single_image": same,
                 "mact_cielab_delta_e_max_cube": round(e_mact[1], 6),
                 "mact_cielab_delta_e_avg_cube": round(e_mact[0], 6),
+                "fitted66_cielab_delta_e_max_cube": round(e_66[1], 8),
+                "fitted66_cielab_delta_e_avg_cube": round(e_66[0], 8),
                 "exact_fp32_cielab_delta_e_max_cube": round(e_exact[1], 8)}
     results = {"served_direct": served(trace, "direct"), "served_staged": served(trace, "staged"),
+               "served_direct_fitted66": served(trace, "direct", h66),
                "plain_exact_per_image": plain(trace), "same_delta_e": same_delta_e(),
                "link": {"d2h_gbs_ring_spread": ring_gbs, "d2h_gbs_ring_start": ring0_gbs}}
     print(json.dumps({"workload": "serve: Poisson 2000 req/s for %g s, 0.1-24 Mpx, pinned host buffers"
