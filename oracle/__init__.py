@@ -77,6 +77,11 @@ def lib():
         L.orc_cube_eps_hsi.argtypes = [_D, ctypes.c_int, _D]
         L.orc_cube_eps_sct.argtypes = [ctypes.POINTER(RGBDef), ctypes.POINTER(SCTCoeffs), _D]
         L.orc_cube_eps_lut.argtypes = [ctypes.POINTER(RGBDef), ctypes.c_int, _F, ctypes.c_int, _D]
+        L.orc_lut_build_hsi.argtypes = [ctypes.c_int, _F]
+        L.orc_lut_interp_hsi_pixel.restype = ctypes.c_double
+        L.orc_lut_interp_hsi_pixel.argtypes = [_F, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.orc_lut_interp_hsi.argtypes = [_F, ctypes.c_int, _U8, ctypes.c_int64, _D, _D, _D, _D, ctypes.c_int]
+        L.orc_cube_eps_hsi_lut.argtypes = [_F, ctypes.c_int, _D]
         L.orc_lab_linear.argtypes = [ctypes.POINTER(RGBDef), ctypes.c_int, _D, ctypes.c_int, _D, ctypes.c_int,
                                      _D, ctypes.c_int64, ctypes.c_int64, _D]
         L.orc_lab_loss_grad.argtypes = [ctypes.POINTER(RGBDef), ctypes.c_int, _D, ctypes.c_int, _D, ctypes.c_int,
@@ -243,6 +248,36 @@ def lut_build(N, rgbdef=None):
     lut = np.empty((N, N, N, 3), dtype=np.float32)
     lib().orc_lut_build(ctypes.byref(d), N, _ptr(lut, _F))
     return lut
+
+
+def lut_build_hsi(N):
+    """N^3 x 3 FP32 LUT of the exact HSI (H, S, I) at nodes k' = i/(N-1),
+    R outermost; H = 0 at gray nodes (S = 0)."""
+    lut = np.empty((N, N, N, 3), dtype=np.float32)
+    lib().orc_lut_build_hsi(N, _ptr(lut, _F))
+    return lut
+
+
+def lut_interp_hsi(lut, rgb, nthreads=0):
+    """Trilinear interpolation of an HSI LUT with angular hue mixing
+    (Eq. equ_angular along B, then G, then R; gray nodes carry no hue).
+    Returns ([H, S, I], cond), cond the smallest mix modulus per pixel."""
+    rgb, npix = _rgb(rgb)
+    lut = np.ascontiguousarray(lut, dtype=np.float32)
+    (H, S, I), _ = _planes(npix, rgb.shape[:-1])
+    cond = np.empty(npix, dtype=np.float64)
+    lib().orc_lut_interp_hsi(_ptr(lut, _F), lut.shape[0], _ptr(rgb, _U8), npix, _ptr(H, _D), _ptr(S, _D),
+                             _ptr(I, _D), _ptr(cond, _D), nthreads)
+    sh = rgb.shape[:-1]
+    return [x.reshape(sh) for x in (H, S, I)], cond.reshape(sh)
+
+
+def cube_eps_hsi_lut(lut):
+    """(eps^T_avg, eps^T_max) in D_HSI of the angular HSI LUT over all 2^24 colours."""
+    lut = np.ascontiguousarray(lut, dtype=np.float32)
+    out = (ctypes.c_double * 2)()
+    lib().orc_cube_eps_hsi_lut(_ptr(lut, _F), lut.shape[0], out)
+    return list(out)
 
 
 def lut_interp(method, lut, rgb, nthreads=0):

@@ -556,6 +556,135 @@ ORC_API void orc_cube_eps_lut(const orc_rgbdef *d, int method, const float *lut,
     out[1] = mx;
 }
 
+/* -------------------------------------- HSI LUT with angular interpolation */
+/* Section "Comparison with 3D Lookup Table Interpolation Methods" (the
+ * closing paragraphs, Eq. equ_angular): interpolating a LUT of an angular
+ * space must mix hues as angles.  Reading (the paper gives the pairwise
+ * formula only): trilinear interpolation where S and I take the trilinear
+ * weights and H is mixed pairwise by Eq. equ_angular along B, then G, then
+ * R, the order of repeated linear interpolation; a gray node (S = 0, hue
+ * undefined) has no hue, so a pair with one gray member takes the other's
+ * angle and a pair of grays stays gray; a result with S = 0 takes H = 0,
+ * the exact transform's convention for grays.  Parity of eps_max unpinned: the
+ * printed maximum comes from antipodal hue pairs mixed at alpha ~ 0.5,
+ * where the formula is ill-conditioned; eps_avg is pinned to 0.3%.
+ *
+ * LUT: node (i, j, k) holds the exact HSI (Eq. equ_rgb_kender) of codes
+ * 255 (i, j, k)/(N-1), each of H, S, I rounded to FP32 (H = 0 at grays).
+ * Layout lut[((i*N + j)*N + k)*3 + c], R outermost. */
+ORC_API void orc_lut_build_hsi(int N, float *lut)
+{
+    double s = 255.0 / (double)(N - 1);
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j)
+            for (int k = 0; k < N; ++k) {
+                double hsi[3];
+                orc_hsi_pixel(0, NULL, 0, i * s, j * s, k * s, hsi);
+                for (int c = 0; c < 3; ++c)
+                    lut[((int64_t)(i * N + j) * N + k) * 3 + c] = (float)hsi[c];
+            }
+}
+
+/* Eq. equ_angular for the pair (h0, h1) at coefficient a, gray members
+ * skipped; *mod receives the modulus of the mixed (cos, sin) sum, the
+ * conditioning of the mix (1 when a member is skipped). */
+static void orc_angle_mix(double h0, int g0, double h1, int g1, double a, double *h, int *g, double *mod)
+{
+    *mod = 1.0;
+    if (g0 && g1) { *h = 0.0; *g = 1; return; }
+    *g = 0;
+    if (g0) { *h = h1; return; }
+    if (g1) { *h = h0; return; }
+    double y = (1.0 - a) * sin(h0) + a * sin(h1);
+    double x = (1.0 - a) * cos(h0) + a * cos(h1);
+    *h = atan2(y, x);
+    *mod = sqrt(x * x + y * y);
+}
+
+/* One pixel: out = (H in [0, 2pi), S, I); returns the smallest mix modulus
+ * met along the chain (small = the hue is ill-conditioned there). */
+ORC_API double orc_lut_interp_hsi_pixel(const float *lut, int N, int r, int g, int b, double out[3])
+{
+    int ir, ig, ib, rr, rg, rb;
+    orc_lut_locate(r, N, &ir, &rr);
+    orc_lut_locate(g, N, &ig, &rg);
+    orc_lut_locate(b, N, &ib, &rb);
+    double f[3] = {rr / 255.0, rg / 255.0, rb / 255.0};   /* R, G, B */
+    int64_t base = ((int64_t)ir * N + ig) * N + ib;
+    double hv[8], sv[8], iv[8];
+    int gv[8];
+    for (int c = 0; c < 8; ++c) {   /* corner c = 4 dR + 2 dG + dB */
+        int64_t node = base + (int64_t)((c >> 2) & 1) * N * N + (int64_t)((c >> 1) & 1) * N + (c & 1);
+        hv[c] = lut[node * 3 + 0];
+        sv[c] = lut[node * 3 + 1];
+        iv[c] = lut[node * 3 + 2];
+        gv[c] = sv[c] == 0.0;
+    }
+    double S = 0.0, I = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        double w = (((c >> 2) & 1) ? f[0] : 1.0 - f[0]) * (((c >> 1) & 1) ? f[1] : 1.0 - f[1]) *
+                   ((c & 1) ? f[2] : 1.0 - f[2]);
+        S += w * sv[c];
+        I += w * iv[c];
+    }
+    double cond = 1.0, m;
+    int n = 8;
+    for (int axis = 2; axis >= 0; --axis) {   /* B (bit 0), then G (bit 1), then R (bit 2) */
+        for (int k = 0; k < n / 2; ++k) {     /* after each pass the survivors are packed */
+            double h;
+            int gg;
+            orc_angle_mix(hv[2 * k], gv[2 * k], hv[2 * k + 1], gv[2 * k + 1], f[axis], &h, &gg, &m);
+            hv[k] = h;
+            gv[k] = gg;
+            if (m < cond) cond = m;
+        }
+        n /= 2;
+    }
+    double H = hv[0];
+    if (H < 0.0) H += 2.0 * ORC_PI;
+    if (H >= 2.0 * ORC_PI) H -= 2.0 * ORC_PI;
+    if (S == 0.0) H = 0.0;   /* a gray result: the exact transform's convention */
+    out[0] = H;
+    out[1] = S;
+    out[2] = I;
+    return cond;
+}
+
+ORC_API void orc_lut_interp_hsi(const float *lut, int N, const uint8_t *rgb, int64_t npix,
+                                double *H, double *S, double *I, double *cond, int nthreads)
+{
+    orc_set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < npix; ++i) {
+        double o[3];
+        double c = orc_lut_interp_hsi_pixel(lut, N, rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2], o);
+        H[i] = o[0];
+        S[i] = o[1];
+        I[i] = o[2];
+        if (cond) cond[i] = c;
+    }
+}
+
+/* eps^T of the angular HSI LUT: D_HSI (Eq. equ_hsi_dist) against the exact
+ * HSI over every 24-bit colour. */
+ORC_API void orc_cube_eps_hsi_lut(const float *lut, int N, double out[2])
+{
+    double sum = 0.0, mx = 0.0;
+#pragma omp parallel for reduction(+:sum) reduction(max:mx) schedule(static)
+    for (int r = 0; r < 256; ++r)
+        for (int g = 0; g < 256; ++g)
+            for (int b = 0; b < 256; ++b) {
+                double e[3], a[3];
+                orc_lut_interp_hsi_pixel(lut, N, r, g, b, a);
+                orc_hsi_pixel(0, NULL, 0, r, g, b, e);
+                double d = orc_d_hsi(e, a);
+                sum += d;
+                if (d > mx) mx = d;
+            }
+    out[0] = sum / 16777216.0;
+    out[1] = mx;
+}
+
 /* ------------------------------------------- differentiable RGB -> CIELAB */
 /* Input is LINEAR RGB (the output of Eq. equ_rgb_lin), planar (N, 3, HW).
  * Lab follows Eq. equ_rgb_xyz and equ_xyz_lab; the loss is the mean over
