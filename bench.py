@@ -526,7 +526,9 @@ def run_grad_workload(args):
 
 def run_lut_workload(args):
     """Standard vs caching LUT layout, 4 methods x {9, 17, 33}^3, on the
-    2^24-colour cube (coherent) and on i.i.d. uniform noise (incoherent)."""
+    2^24-colour cube (coherent) and on i.i.d. uniform noise (incoherent); and
+    HSI through a 17^3 / 33^3 LUT with angular hue interpolation beside the
+    exact and MACT HSI transforms."""
     import numpy as np
     import torch
     from paper_1009_0854_gb300 import mact, synth
@@ -561,7 +563,36 @@ def run_lut_workload(args):
                     ms = a.elapsed_time(b) / args.steps
                     rows["%s_lut%d_%s_%s" % (name, n, m, layout)] = {
                         "gpix_s": round(PIX / ms / 1e6, 1), "hbm_frac": round(PIX * 15 / (ms * 1e-3) / 1e9 / hbm, 4)}
-    print(json.dumps({"workload": "lut: standard vs caching layout, cube and uniform noise, 2^24 px", "rows": rows}))
+
+    def timed(fn, xs):
+        for i in range(3):
+            fn(xs[i % 4])
+        torch.cuda.synchronize()
+        a, b = _events(torch)
+        a.record()
+        for i in range(args.steps):
+            fn(xs[i % 4])
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps
+
+    # HSI through a LUT with angular hue interpolation (the paper's trilinear
+    # case) beside the exact and MACT HSI transforms on the same input
+    he = mact.mact_create(exact=1)
+    out3 = out.view(3, 4096, 4096)
+    for name, x in inputs.items():
+        xs = [x.clone() for _ in range(4)]
+        for n in (17, 33):
+            lut4 = mact.mact_lut_build_hsi(h, n)
+            ms = timed(lambda v: mact.mact_lut_interp_hsi(h, lut4, v, out=out), xs)
+            rows["%s_hsi_angular_lut%d_trilinear" % (name, n)] = {
+                "gpix_s": round(PIX / ms / 1e6, 1), "hbm_frac": round(PIX * 15 / (ms * 1e-3) / 1e9 / hbm, 4)}
+        for hn, hh in (("exact", he), ("mact", h)):
+            ms = timed(lambda v: mact.mact_convert(hh, v, "hsi", out=out3), xs)
+            rows["%s_hsi_%s" % (name, hn)] = {
+                "gpix_s": round(PIX / ms / 1e6, 1), "hbm_frac": round(PIX * 15 / (ms * 1e-3) / 1e9 / hbm, 4)}
+    print(json.dumps({"workload": "lut: standard vs caching layout, cube and uniform noise, 2^24 px; HSI through "
+                      "an angular-hue LUT vs the exact and MACT HSI transforms", "rows": rows}))
 
 
 class PinnedRing:

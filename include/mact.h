@@ -404,6 +404,30 @@ mact_status mact_lut_interp_cached(mact_handle h, int32_t method, const float *d
                                    const uint8_t *d_rgb, int64_t npix, float *const d_out[3], int32_t *d_sel,
                                    mact_stream stream);
 
+/* ---- HSI LUT with angular hue interpolation -----------------------------
+ * The closing paragraphs of Section "Comparison with 3D Lookup Table
+ * Interpolation Methods": a LUT of an angular space must mix hues as angles,
+ * Eq. equ_angular, theta = atan2((1-a) sin t0 + a sin t1, (1-a) cos t0 +
+ * a cos t1); the paper reports trilinear HSI interpolation built on it.  The
+ * paper states the pairwise formula only; here S and I take the trilinear
+ * weights and H is mixed pairwise along B, then G, then R, a gray node
+ * (S = 0) carrying no hue (its pair takes the other angle), and a result with
+ * S = 0 takes H = 0.  A pair of antipodal hues mixed near a = 0.5 has no
+ * direction and is treated as gray. */
+
+/* Build the n^3-node HSI LUT (2 <= n <= 64) at k' = (i, j, k)/(n-1), R
+ * outermost: node = float4 (cos H, sin H, S, I) of the exact HSI
+ * (Eq. equ_rgb_kender), each of H, S, I rounded to FP32 first; gray nodes
+ * hold (0, 0, 0, I).  d_lut4: n^3 * 4 floats, 16-byte aligned. */
+mact_status mact_lut_build_hsi(mact_handle h, int32_t n, float *d_lut4, mact_stream stream);
+
+/* Trilinear interpolation of npix interleaved uint8 pixels in an HSI LUT
+ * built by mact_lut_build_hsi: d_out[0] = H (radians, [0, 2 pi)),
+ * d_out[1] = S, d_out[2] = I, FP32 planes of npix elements (4-byte aligned).
+ * Cells are selected by the same integer extraction as mact_lut_interp. */
+mact_status mact_lut_interp_hsi(mact_handle h, const float *d_lut4, int32_t n, const uint8_t *d_rgb, int64_t npix,
+                                float *const d_out[3], mact_stream stream);
+
 /* Which host memory the kernels of handle h may be given (the paper has no
  * counterpart: it concerns where the pixels live, not how they are
  * converted).  Returns 1 when the device addresses any host memory through

@@ -642,6 +642,37 @@ mact_status mact_lut_interp_cached(mact_handle h, int32_t method, const float *d
                        "mact_lut_interp_cached");
 }
 
+mact_status mact_lut_build_hsi(mact_handle h, int32_t n, float *d_lut4, mact_stream stream)
+{
+    if (!h) return inval("mact_lut_build_hsi: NULL handle");
+    if (n < 2 || n > 64) return inval("LUT size must be 2..64");
+    if (!d_lut4) return inval("d_lut4 is NULL");
+    if ((reinterpret_cast<uintptr_t>(d_lut4) & 15) != 0) return inval("d_lut4 must be 16-byte aligned");
+    mact_status st = check_access(*h, d_lut4, "d_lut4");
+    if (st != MACT_OK) return st;
+    return cuda_status(launch_lut_build_hsi(n, reinterpret_cast<float4 *>(d_lut4), (cudaStream_t)stream),
+                       "mact_lut_build_hsi");
+}
+
+mact_status mact_lut_interp_hsi(mact_handle h, const float *d_lut4, int32_t n, const uint8_t *d_rgb, int64_t npix,
+                                float *const d_out[3], mact_stream stream)
+{
+    if (!h) return inval("mact_lut_interp_hsi: NULL handle");
+    if (n < 2 || n > 64) return inval("LUT size must be 2..64");
+    if (npix < 0 || npix > (int64_t(1) << 42)) return inval("pixel count out of range");
+    if (npix == 0) return MACT_OK;
+    if (!d_lut4 || !d_rgb || !d_out || !d_out[0] || !d_out[1] || !d_out[2]) return inval("NULL pointer");
+    if ((reinterpret_cast<uintptr_t>(d_lut4) & 15) != 0) return inval("d_lut4 must be 16-byte aligned");
+    if (!aligned4(d_out[0]) || !aligned4(d_out[1]) || !aligned4(d_out[2])) return inval("d_out[] must be 4-byte aligned");
+    mact_status st = check_access(*h, d_lut4, "d_lut4");
+    if (st == MACT_OK) st = check_access(*h, d_rgb, "d_rgb");
+    for (int c = 0; c < 3 && st == MACT_OK; ++c) st = check_access(*h, d_out[c], "d_out");
+    if (st != MACT_OK) return st;
+    return cuda_status(launch_lut_interp_hsi(*h, reinterpret_cast<const float4 *>(d_lut4), n, d_rgb, npix, d_out,
+                                             (cudaStream_t)stream),
+                       "mact_lut_interp_hsi");
+}
+
 int32_t mact_host_memory_access(mact_handle h)
 {
     if (!h) return inval("mact_host_memory_access: NULL handle");

@@ -84,6 +84,12 @@ cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut,
                               int32_t *d_sel, const float4 *d_lut4, cudaStream_t s);
 cudaError_t launch_lut_pack4(const float *d_lut, int n, float4 *d_lut4, cudaStream_t s);
 cudaError_t launch_lut_cache_build(const float *d_lut, int n, float4 *d_cache, cudaStream_t s);
+
+// k_lut_hsi.cu: HSI LUT of (cos H, sin H, S, I) nodes, trilinear with the
+// angular hue mix
+cudaError_t launch_lut_build_hsi(int n, float4 *d_lut4, cudaStream_t s);
+cudaError_t launch_lut_interp_hsi(const mact_ctx &h, const float4 *d_lut4, int n, const uint8_t *d_rgb,
+                                  int64_t npix, float *const out[3], cudaStream_t s);
 cudaError_t launch_lut_interp_cached(const mact_ctx &h, int method, const float4 *d_cache, int n,
                                      const uint8_t *d_rgb, int64_t npix, float *const out[3], int32_t *d_sel,
                                      cudaStream_t s);

@@ -146,6 +146,10 @@ def lib():
         L.mact_strerror.restype = ctypes.c_char_p
         L.mact_last_error.argtypes = []
         L.mact_last_error.restype = ctypes.c_char_p
+        L.mact_lut_build_hsi.argtypes = [_VP, ctypes.c_int32, _VP, _VP]
+        L.mact_lut_build_hsi.restype = ctypes.c_int
+        L.mact_lut_interp_hsi.argtypes = [_VP, _VP, ctypes.c_int32, _VP, ctypes.c_int64, ctypes.POINTER(_VP), _VP]
+        L.mact_lut_interp_hsi.restype = ctypes.c_int
         L.mact_host_memory_access.argtypes = [_VP]
         L.mact_host_memory_access.restype = ctypes.c_int32
         for name in ("mact_create", "mact_destroy", "mact_convert", "mact_convert_batch", "mact_convert_batch_static",
@@ -557,6 +561,32 @@ def mact_lut_interp_cached(h, method, cache, n, rgb, out=None, sel=False, stream
                                         ctypes.byref(ptrs), _VP(s.data_ptr() if s is not None else 0),
                                         _stream(stream)), "mact_lut_interp_cached")
     return (out, s) if sel else out
+
+
+def mact_lut_build_hsi(h, n, out=None, device="cuda", stream=None):
+    """(n, n, n, 4) FP32 HSI LUT: (cos H, sin H, S, I) of the exact HSI at the
+    nodes (gray nodes: (0, 0, 0, I))."""
+    if out is None:
+        out = torch.empty((n, n, n, 4), dtype=torch.float32, device=device)
+    _check(lib().mact_lut_build_hsi(h.ptr, n, _VP(out.data_ptr()), _stream(stream)), "mact_lut_build_hsi")
+    return out
+
+
+def mact_lut_interp_hsi(h, lut4, rgb, out=None, stream=None):
+    """Trilinear HSI interpolation with angular hue mixing of the (npix, 3)
+    or (H, W, 3) uint8 pixels of rgb.  Returns (3, npix) planes H, S, I."""
+    if lut4.dtype != torch.float32 or not lut4.is_contiguous() or lut4.dim() != 4 or lut4.shape[3] != 4:
+        raise ValueError("lut4 must be a contiguous (n, n, n, 4) float32 tensor")
+    if rgb.dtype != torch.uint8 or not rgb.is_contiguous() or rgb.shape[-1] != 3:
+        raise ValueError("rgb must be a contiguous (..., 3) uint8 tensor")
+    npix = rgb.numel() // 3
+    if out is None:
+        out = torch.empty((3, npix), dtype=torch.float32, device=rgb.device,
+                          pin_memory=rgb.device.type == "cpu")
+    ptrs = (_VP * 3)(*(out[c].data_ptr() for c in range(3)))
+    _check(lib().mact_lut_interp_hsi(h.ptr, _VP(lut4.data_ptr()), lut4.shape[0], _VP(rgb.data_ptr()), npix, ptrs,
+                                     _stream(stream)), "mact_lut_interp_hsi")
+    return out
 
 
 def mact_host_memory_access(h):
