@@ -329,7 +329,12 @@ typedef struct {
 /* Create a server for handle h (on h's device), in direct mode.  max_slots
  * bounds the number of admitted, unfinished requests (1..65536);
  * mem_budget_bytes (>= 4096) bounds their staging memory.  Device-resident
- * inputs and outputs, and host buffers used in place, take no budget. */
+ * inputs and outputs, and host buffers used in place, take no budget.
+ * A tick that fails leaves its requests failed (MACT_E_CUDA from poll and
+ * wait, with the reason in mact_last_error) and returns their staging
+ * memory once the server's streams have drained.  For testing that path,
+ * the environment variable MACT_SERVE_FAIL_EVERY=k, read here, fails every
+ * k-th batch on the host after its input copies are enqueued. */
 mact_status mact_serve_create(mact_handle h, size_t mem_budget_bytes, int32_t max_slots, mact_server_t *out);
 
 /* How host buffers of requests submitted from now on are used:

@@ -26,11 +26,13 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -76,6 +78,7 @@ struct Request {
     Clock::time_point t_submit, t_admit, t_done;
     int state = kQueued;
     int64_t pixels = 0;
+    std::string err;                   // why the request failed (reported by poll and wait)
 };
 
 // First-fit allocator over [0, size) in 256-byte units.
@@ -151,6 +154,8 @@ struct mact_server {
     size_t budget = 0;
     int max_slots = 0;
     int mode = MACT_SERVE_DIRECT;          // how host buffers of new requests are used
+    int fail_every = 0;                    // host-side fault injection (tests): fail every k-th batch
+    int64_t batches_started = 0;
     void *arena_base = nullptr;
     Arena arena;
     cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
@@ -181,11 +186,32 @@ namespace mact {
 
 static void fail_locked(mact_server *s, Request *r, const char *what, cudaError_t e)
 {
-    (void)what;
-    (void)e;
     r->state = kFailed;
     r->t_done = Clock::now();
+    r->err = std::string(what) + (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : std::string());
     s->failed++;
+}
+
+// Wait, with a bound, until the server's three streams (which only the
+// scheduler thread feeds) have drained; true if they all have.  After a
+// failed tick, arena ranges are released only then: a range whose copies or
+// kernel cannot be shown complete is leaked rather than reused under work in
+// flight.
+static bool streams_drained_within(const mact_server *s, double ms)
+{
+    const auto t0 = Clock::now();
+    const cudaStream_t st[3] = {s->s_h2d, s->s_comp, s->s_d2h};
+    for (int k = 0; k < 3;) {
+        const cudaError_t q = cudaStreamQuery(st[k]);
+        if (q == cudaSuccess) { ++k; continue; }
+        if (q != cudaErrorNotReady) {
+            cudaGetLastError();
+            return false;
+        }
+        if (ms_since(t0, Clock::now()) > ms) return false;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    return true;
 }
 
 // One scheduler tick: admit, launch, retire.  Returns true if it did work.
@@ -246,7 +272,15 @@ static bool serve_tick(mact_server *s)
         if (e == cudaSuccess) e = cudaEventRecord(bev->in, s->s_h2d);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s->s_comp, bev->in, 0);
         mact_status st = MACT_OK;
-        if (e == cudaSuccess) st = mact_convert_batch(s->h, imgs.data(), (int32_t)imgs.size(), s->s_comp);
+        bool injected = false;
+        if (e == cudaSuccess) {
+            if (s->fail_every > 0 && ++s->batches_started % s->fail_every == 0) {
+                st = MACT_E_NOMEM;   // injected on the host, after the input copies are enqueued
+                injected = true;
+            } else {
+                st = mact_convert_batch(s->h, imgs.data(), (int32_t)imgs.size(), s->s_comp);
+            }
+        }
         if (e == cudaSuccess && st == MACT_OK) e = cudaEventRecord(bev->comp, s->s_comp);
         if (e == cudaSuccess && st == MACT_OK) e = cudaStreamWaitEvent(s->s_d2h, bev->comp, 0);
         for (Request *r : batch) {
@@ -277,22 +311,29 @@ static bool serve_tick(mact_server *s)
             if (e == cudaSuccess) e = cudaEventRecord(r->ev_done, s->s_d2h);
             r->bev = bev;
         }
+        const bool failed = e != cudaSuccess || st != MACT_OK;
+        // on failure, copies or the kernel already enqueued may still touch
+        // the batch's arena ranges: release them only once the streams have
+        // drained (bounded wait, outside the lock)
+        const bool releasable = !failed || streams_drained_within(s, 5000.0);
         std::unique_lock<std::mutex> lk(s->mu);
         s->batches++;
         for (Request *r : batch) {
-            if (e != cudaSuccess || st != MACT_OK || !r->ev_done) {
-                fail_locked(s, r, "serve", e);
+            if (failed || !r->ev_done) {
+                fail_locked(s, r,
+                            injected ? "mact_serve: batched conversion failed (injected)"
+                                     : (st != MACT_OK ? "mact_serve: batched conversion failed" : "mact_serve"),
+                            e);
                 if (r->ev_out) cudaEventDestroy(r->ev_out);
                 if (r->ev_done) cudaEventDestroy(r->ev_done);
                 r->ev_out = r->ev_done = nullptr;
                 r->bev.reset();
-                s->arena.release(r->off, r->len);
-                if (e != cudaSuccess) set_error(std::string("mact_serve: ") + cudaGetErrorString(e));
+                if (releasable) s->arena.release(r->off, r->len);
             } else {
                 s->inflight.push_back(r);
             }
         }
-        if (e != cudaSuccess || st != MACT_OK) s->cv_done.notify_all();
+        if (failed) s->cv_done.notify_all();
     }
     // retire: every request's completion event is recorded on the one D2H
     // stream, so they fire in admission order; query the oldest only
@@ -326,7 +367,7 @@ static bool serve_tick(mact_server *s)
             if (!s->any_done) { s->t_first = r->t_submit; s->any_done = true; }
             s->t_last = r->t_done;
         } else {
-            fail_locked(s, r, "serve", q);
+            fail_locked(s, r, "mact_serve: conversion or output copy failed", q);
         }
         cudaEventDestroy(r->ev_done);
         r->ev_done = nullptr;
@@ -387,6 +428,7 @@ mact_status mact_serve_create(mact_handle h, size_t mem_budget_bytes, int32_t ma
         return st;
     }
     s->arena.reset(s->budget);
+    if (const char *k = std::getenv("MACT_SERVE_FAIL_EVERY")) s->fail_every = std::atoi(k);
     s->worker = std::thread(serve_loop, s);
     *out = s;
     return MACT_OK;
@@ -472,7 +514,10 @@ mact_status mact_serve_poll(mact_server_t s, uint64_t ticket, int32_t *done, dou
     Request *r = it->second;
     *done = (r->state == kDone || r->state == kFailed || r->state == kCancelled) ? 1 : 0;
     if (latency_ms) *latency_ms = *done ? ms_since(r->t_submit, r->t_done) : 0.0;
-    if (r->state == kFailed) return MACT_E_CUDA;
+    if (r->state == kFailed) {
+        set_error(r->err);
+        return MACT_E_CUDA;
+    }
     return MACT_OK;
 }
 
@@ -489,7 +534,11 @@ mact_status mact_serve_wait(mact_server_t s, uint64_t ticket, double timeout_ms,
         return MACT_E_TIMEOUT;
     }
     if (latency_ms) *latency_ms = ms_since(r->t_submit, r->t_done);
-    return r->state == kFailed ? MACT_E_CUDA : MACT_OK;
+    if (r->state == kFailed) {
+        set_error(r->err);
+        return MACT_E_CUDA;
+    }
+    return MACT_OK;
 }
 
 mact_status mact_serve_cancel(mact_server_t s, uint64_t ticket)

@@ -166,3 +166,36 @@ def test_direct_and_staged_modes_agree(h):
         with pytest.raises(mact.MactError):
             mact.mact_serve_set_mode(srv, 7)
         srv.close()
+
+
+def test_failed_batches_report_and_return_their_memory(h, monkeypatch):
+    """Host-side fault injection (every 3rd batch fails after its input
+    copies are enqueued): failed requests report MACT_E_CUDA with the reason,
+    the others still equal mact_convert, and the staging memory of the failed
+    ones comes back (a request needing most of the budget is admitted)."""
+    monkeypatch.setenv("MACT_SERVE_FAIL_EVERY", "3")
+    srv = mact.mact_serve_create(h, 8 << 20, max_slots=4)
+    monkeypatch.delenv("MACT_SERVE_FAIL_EVERY")
+    mact.mact_serve_set_mode(srv, "staged")
+    reqs = _requests(11, 12, lo=16, hi=300)
+    refs = _reference(h, reqs)
+    failed = 0
+    for k, ((im, space, dt), ref) in enumerate(zip(reqs, refs)):
+        t, out = mact.mact_serve_submit(srv, torch.from_numpy(im).pin_memory(), space, dtype=dt)
+        try:
+            mact.mact_serve_wait(srv, t, 30000)
+            assert torch.equal(out, ref)
+        except mact.MactError as e:
+            assert e.status == mact.MACT_E_CUDA and "injected" in str(e)
+            failed += 1
+        mact.mact_serve_release(srv, t)
+    assert failed == 4
+    st = mact.mact_serve_stats(srv)
+    assert st["failed"] == 4 and st["completed"] == 8
+    big = torch.from_numpy(synth.gradient_noise_image(700, 700, seed=9)).pin_memory()   # 1.5 + 5.9 MB of 8 MB
+    for _ in range(2):                 # the 3rd batch after this point would fail: stop before it
+        t, out = mact.mact_serve_submit(srv, big, "cielab")
+        mact.mact_serve_wait(srv, t, 30000)
+        assert torch.equal(out, mact.mact_convert(h, big.cuda(), "cielab").cpu())
+        mact.mact_serve_release(srv, t)
+    srv.close()
