@@ -64,19 +64,25 @@ __device__ __forceinline__ void locate(uint32_t v, int n, int &idx, float &f)
     f = (float)rem * (1.0f / 255.0f);
 }
 
-// Eq. equ_angular on unit vectors, gray (zero) members skipped.
+// Eq. equ_angular on unit vectors, gray (zero) members skipped.  The gray
+// rule only changes the result when the mixed vector vanishes (a = 0 or 1
+// against a gray member, both gray, or antipodal hues), so it is tested on
+// that path alone; elsewhere normalising the mix gives the other member's
+// direction to rounding.
 __device__ __forceinline__ float2 angle_mix(float2 u0, float2 u1, float a)
 {
-    const bool g0 = u0.x == 0.0f && u0.y == 0.0f;
-    const bool g1 = u1.x == 0.0f && u1.y == 0.0f;
-    if (g0) return u1;          // (both gray: u1 is the zero vector)
-    if (g1) return u0;
     const float x = fmaf(a, u1.x - u0.x, u0.x);
     const float y = fmaf(a, u1.y - u0.y, u0.y);
     const float m2 = fmaf(x, x, y * y);
-    if (!(m2 > 1e-30f)) return make_float2(0.0f, 0.0f);
-    const float r = rsqrtf(m2);
-    return make_float2(x * r, y * r);
+    if (m2 > 1e-30f) {
+        const float r = rsqrtf(m2);
+        return make_float2(x * r, y * r);
+    }
+    const bool g0 = u0.x == 0.0f && u0.y == 0.0f;
+    const bool g1 = u1.x == 0.0f && u1.y == 0.0f;
+    if (g0) return u1;
+    if (g1) return u0;
+    return make_float2(0.0f, 0.0f);
 }
 
 template <int N>
