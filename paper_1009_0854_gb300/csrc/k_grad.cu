@@ -225,11 +225,44 @@ __global__ void k_sum_partials(const double *__restrict__ partial, int n, double
     if (threadIdx.x == 0) *out = (float)(red[0] * scale);
 }
 
-static int grad_grid(const mact_ctx &h, uint32_t items)
+// One wave of the kernel's resident CTAs (grid-stride loops inside): a grid
+// larger than what fits leaves a second, partly empty wave.  occ <= 8, so the
+// grid never exceeds the num_sms * 8 loss partials.
+static int grad_grid(const mact_ctx &h, uint32_t items, int occ)
 {
     const int64_t g = ((int64_t)items + kGradThreads - 1) / kGradThreads;
-    const int64_t cap = (int64_t)h.num_sms * 8;   // 8 resident 256-thread CTAs per SM
+    const int64_t cap = (int64_t)h.num_sms * (occ < 8 ? occ : 8);
     return (int)(g < cap ? (g > 0 ? g : 1) : cap);
+}
+
+// resident CTAs per SM of one kernel instantiation (thread-safe one-time init)
+template <class K>
+static int occupancy(K kern)
+{
+    int o = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kGradThreads, 0);
+    return (e != cudaSuccess || o <= 0) ? 1 : o;
+}
+
+template <int FORM, bool VEC>
+static int occ_forward()
+{
+    static const int o = occupancy(k_lab_forward<FORM, VEC>);
+    return o;
+}
+
+template <int FORM, bool VEC>
+static int occ_backward()
+{
+    static const int o = occupancy(k_lab_backward<FORM, VEC>);
+    return o;
+}
+
+template <int FORM, bool GRAD, bool VEC>
+static int occ_delta_e()
+{
+    static const int o = occupancy(k_lab_delta_e<FORM, GRAD, VEC>);
+    return o;
 }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
@@ -260,20 +293,22 @@ cudaError_t launch_lab_forward(const mact_ctx &h, const float *x, int64_t nb, in
 {
     const bool v = use_vec(hw, {x, lab});
     const Geometry g = geometry(nb, hw, v);
-    const int grid = grad_grid(h, g.items);
+#define MACT_FWD(F, V) \
+    k_lab_forward<F, V><<<grad_grid(h, g.items, occ_forward<F, V>()), kGradThreads, 0, s>>>(x, g, lab, h.co)
     switch (grad_form(h)) {
     case 0:
-        if (v) k_lab_forward<0, true><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
-        else k_lab_forward<0, false><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
+        if (v) MACT_FWD(0, true);
+        else MACT_FWD(0, false);
         break;
     case 6:
-        if (v) k_lab_forward<6, true><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
-        else k_lab_forward<6, false><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
+        if (v) MACT_FWD(6, true);
+        else MACT_FWD(6, false);
         break;
     default:
-        if (v) k_lab_forward<4, true><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
-        else k_lab_forward<4, false><<<grid, kGradThreads, 0, s>>>(x, g, lab, h.co);
+        if (v) MACT_FWD(4, true);
+        else MACT_FWD(4, false);
     }
+#undef MACT_FWD
     return cudaGetLastError();
 }
 
@@ -282,31 +317,40 @@ cudaError_t launch_lab_backward(const mact_ctx &h, const float *x, const float *
 {
     const bool v = use_vec(hw, {x, glab, gx});
     const Geometry g = geometry(nb, hw, v);
-    const int grid = grad_grid(h, g.items);
+#define MACT_BWD(F, V) \
+    k_lab_backward<F, V><<<grad_grid(h, g.items, occ_backward<F, V>()), kGradThreads, 0, s>>>(x, glab, g, gx, h.co)
     switch (grad_form(h)) {
     case 0:
-        if (v) k_lab_backward<0, true><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
-        else k_lab_backward<0, false><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
+        if (v) MACT_BWD(0, true);
+        else MACT_BWD(0, false);
         break;
     case 6:
-        if (v) k_lab_backward<6, true><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
-        else k_lab_backward<6, false><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
+        if (v) MACT_BWD(6, true);
+        else MACT_BWD(6, false);
         break;
     default:
-        if (v) k_lab_backward<4, true><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
-        else k_lab_backward<4, false><<<grid, kGradThreads, 0, s>>>(x, glab, g, gx, h.co);
+        if (v) MACT_BWD(4, true);
+        else MACT_BWD(4, false);
     }
+#undef MACT_BWD
     return cudaGetLastError();
 }
 
+// returns the grid it launched (the number of loss partials written)
 template <int FORM>
-static void delta_e_launch(bool grad, bool v, int grid, cudaStream_t s, const float *x, const float *tgt,
-                           const Geometry &g, float inv, float *gx, double *partial, const Coeffs &co)
+static int delta_e_launch(const mact_ctx &h, bool grad, bool v, cudaStream_t s, const float *x, const float *tgt,
+                          const Geometry &g, float inv, float *gx, double *partial, const Coeffs &co)
 {
-    if (grad && v) k_lab_delta_e<FORM, true, true><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co);
-    else if (grad) k_lab_delta_e<FORM, true, false><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co);
-    else if (v) k_lab_delta_e<FORM, false, true><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co);
-    else k_lab_delta_e<FORM, false, false><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co);
+    int grid;
+#define MACT_DE(G, V)                                                                          \
+    grid = grad_grid(h, g.items, occ_delta_e<FORM, G, V>());                                   \
+    k_lab_delta_e<FORM, G, V><<<grid, kGradThreads, 0, s>>>(x, tgt, g, inv, gx, partial, co)
+    if (grad && v) { MACT_DE(true, true); }
+    else if (grad) { MACT_DE(true, false); }
+    else if (v) { MACT_DE(false, true); }
+    else { MACT_DE(false, false); }
+#undef MACT_DE
+    return grid;
 }
 
 cudaError_t launch_lab_delta_e(const mact_ctx &h, const float *x, const float *tgt, int64_t nb, int64_t hw,
@@ -315,12 +359,12 @@ cudaError_t launch_lab_delta_e(const mact_ctx &h, const float *x, const float *t
     // partial holds num_sms * 8 entries, the largest grid grad_grid returns
     const bool v = use_vec(hw, {x, tgt, gx});
     const Geometry g = geometry(nb, hw, v);
-    const int grid = grad_grid(h, g.items);
     const float inv = (float)(1.0 / (double)(nb * hw));
+    int grid;
     switch (grad_form(h)) {
-    case 0: delta_e_launch<0>(gx != nullptr, v, grid, s, x, tgt, g, inv, gx, partial, h.co); break;
-    case 6: delta_e_launch<6>(gx != nullptr, v, grid, s, x, tgt, g, inv, gx, partial, h.co); break;
-    default: delta_e_launch<4>(gx != nullptr, v, grid, s, x, tgt, g, inv, gx, partial, h.co);
+    case 0: grid = delta_e_launch<0>(h, gx != nullptr, v, s, x, tgt, g, inv, gx, partial, h.co); break;
+    case 6: grid = delta_e_launch<6>(h, gx != nullptr, v, s, x, tgt, g, inv, gx, partial, h.co); break;
+    default: grid = delta_e_launch<4>(h, gx != nullptr, v, s, x, tgt, g, inv, gx, partial, h.co);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
