@@ -80,3 +80,38 @@ def test_strerror(L):
     assert mact.mact_strerror(-1) == "invalid argument"
     assert mact.mact_strerror(-2).startswith("out of memory")
     assert mact.mact_strerror(-5) == "timed out"
+
+
+def test_config_default_uses_the_printed_cube_root(L):
+    from paper_1009_0854_gb300 import mact
+    assert mact.mact_config_default().lab_coeffs == 0
+
+
+@pytest.mark.parametrize("fields", [dict(lab_coeffs=2), dict(lab_coeffs=1, lab_n=7, lab_m=6),
+                                    dict(lab_coeffs=1, lab_n=6, lab_m=0), dict(lab_coeffs=-1)])
+def test_create_rejects_bad_fitted_rational_config(L, fields):
+    from paper_1009_0854_gb300 import mact
+    cfg = mact.mact_config_default(**fields)
+    h = ctypes.c_void_p()
+    assert L.mact_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+    assert h.value is None
+
+
+def test_fitted_rational_fit_runs_on_the_host(L):
+    """The (6,6) Remez fit happens on the host before any CUDA call: without
+    a GPU mact_create gets past it and fails only at the device (MACT_E_CUDA),
+    never with MACT_E_UNSUPPORTED (a fit that did not converge)."""
+    from paper_1009_0854_gb300 import mact
+    for n, m in [(6, 6), (5, 6), (1, 1)]:
+        cfg = mact.mact_config_default(lab_coeffs=1, lab_n=n, lab_m=m)
+        h = ctypes.c_void_p()
+        st = L.mact_create(ctypes.byref(cfg), ctypes.byref(h))
+        assert st in (0, -3), (n, m, st)
+        if st == 0:
+            L.mact_destroy(h)
+
+
+def test_newest_entry_points_reject_null(L):
+    assert L.mact_host_memory_access(None) == -1
+    assert L.mact_serve_set_mode(None, 0) == -1
+    assert L.mact_lut_build_hsi(None, 17, None, None) == -1
