@@ -386,7 +386,7 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-# ------------------------------------------------ other workloads (reported in the design doc)
+# ------------------------------------------------ other workloads (--workload; one JSON line each)
 
 def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
