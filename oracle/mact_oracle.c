@@ -30,6 +30,11 @@
  *    code v is idx = v(N-1) div 255 with remainder rem = v(N-1) mod 255,
  *    except v = 255 which uses idx = N-2, rem = 255.  Simplex choice compares
  *    the integer remainders.
+ *
+ * Parity unpinned: the HSI average cube error (orc_cube_eps_hsi; 1-3% from
+ * the printed averages) and the angular HSI LUT's maximum cube error
+ * (orc_cube_eps_hsi_lut).  Parity partial: the pyramidal LUT's average cube
+ * error (within 0.07%; its maxima are exact).  Everything else is pinned.
  */
 #include <math.h>
 #include <stdint.h>
@@ -567,7 +572,8 @@ ORC_API void orc_cube_eps_lut(const orc_rgbdef *d, int method, const float *lut,
  * angle and a pair of grays stays gray; a result with S = 0 takes H = 0,
  * the exact transform's convention for grays.  Parity of eps_max unpinned: the
  * printed maximum comes from antipodal hue pairs mixed at alpha ~ 0.5,
- * where the formula is ill-conditioned; eps_avg is pinned to 0.3%.
+ * where the formula is ill-conditioned; eps_avg is pinned within 0.5%
+ * (it lands 0.3% away).
  *
  * LUT: node (i, j, k) holds the exact HSI (Eq. equ_rgb_kender) of codes
  * 255 (i, j, k)/(N-1), each of H, S, I rounded to FP32 (H = 0 at grays).
