@@ -171,6 +171,17 @@ def _check(st, where):
         raise MactError(st, where, lib().mact_last_error().decode())
 
 
+def _need(t, name, shape, dtype=torch.float32):
+    """Refuse a caller-supplied tensor whose size, type or layout differs from
+    what the kernel will read or write (the C ABI cannot see buffer sizes)."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous %s tensor of shape %s (got %s %s%s)" % (
+            name, dtype, tuple(shape), t.dtype, tuple(t.shape), "" if t.is_contiguous() else ", strided"))
+    return t
+
+
 def _stream(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -230,6 +241,8 @@ def _image(rgb, space, out):
         raise ValueError("rgb pixels must be interleaved and rows dense (stride (pitch, 3, 1))")
     if out.dim() != 3 or out.shape[0] != 3 or out.shape[1:] != rgb.shape[:2]:
         raise ValueError("out must have shape (3, H, W)")
+    if out.dtype not in DTYPES:
+        raise ValueError("out must be float32 or float16")
     if out.stride(2) != 1:
         raise ValueError("out rows must be dense")
     H, W = rgb.shape[0], rgb.shape[1]
@@ -263,6 +276,8 @@ def mact_convert_batch(h, images, dtype=torch.float32, outs=None, stream=None):
     if outs is None:
         outs = [torch.empty((3, r.shape[0], r.shape[1]), dtype=dtype, device=r.device,
                          pin_memory=r.device.type == "cpu") for r, _ in images]
+    if len(outs) != n:
+        raise ValueError("outs must hold one output per image")
     arr = (Image * max(n, 1))()
     for i, ((rgb, space), out) in enumerate(zip(images, outs)):
         arr[i] = _image(rgb, space, out)
@@ -278,6 +293,8 @@ def mact_convert_batch_static(h, images, dtype=torch.float32, outs=None, stream=
     if outs is None:
         outs = [torch.empty((3, r.shape[0], r.shape[1]), dtype=dtype, device=r.device,
                          pin_memory=r.device.type == "cpu") for r, _ in images]
+    if len(outs) != n:
+        raise ValueError("outs must hold one output per image")
     arr = (Image * max(n, 1))()
     for i, ((rgb, space), out) in enumerate(zip(images, outs)):
         arr[i] = _image(rgb, space, out)
@@ -289,6 +306,7 @@ def mact_lut_build(h, n, out=None, device="cuda", stream=None):
     """n^3 x 3 FP32 LUT of the exact CIELAB at the lattice nodes."""
     if out is None:
         out = torch.empty((n, n, n, 3), dtype=torch.float32, device=device)
+    _need(out, "out", (n, n, n, 3))
     _check(lib().mact_lut_build(h.ptr, n, _VP(out.data_ptr()), _stream(stream)), "mact_lut_build")
     return out
 
@@ -302,10 +320,13 @@ def mact_lut_interp(h, method, lut, rgb, out=None, sel=False, stream=None):
     if rgb.dtype != torch.uint8 or not rgb.is_contiguous() or rgb.shape[-1] != 3:
         raise ValueError("rgb must be a contiguous (..., 3) uint8 tensor")
     n = lut.shape[0]
+    if lut.shape[1] != n or lut.shape[2] != n:
+        raise ValueError("lut must be a cube (n, n, n, 3)")
     npix = rgb.numel() // 3
     if out is None:
         out = torch.empty((3, npix), dtype=torch.float32, device=rgb.device,
                           pin_memory=rgb.device.type == "cpu")
+    _need(out, "out", (3, npix))
     ptrs = (_VP * 3)(*(out[c].data_ptr() for c in range(3)))
     s = (torch.empty(npix, dtype=torch.int32, device=rgb.device, pin_memory=rgb.device.type == "cpu")
          if sel else None)
@@ -328,6 +349,8 @@ def mact_cube_error(h, space):
 
 def mact_cube_error_lut(h, method, lut):
     """(eps_avg, eps_max) of LUT interpolation over all 2^24 colours."""
+    n = lut.shape[0] if isinstance(lut, torch.Tensor) and lut.dim() == 4 else 0
+    _need(lut, "lut", (n, n, n, 3))
     a, m = ctypes.c_double(), ctypes.c_double()
     md = METHODS[method] if isinstance(method, str) else int(method)
     _check(lib().mact_cube_error_lut(h.ptr, md, _VP(lut.data_ptr()), lut.shape[0], ctypes.byref(a),
@@ -338,6 +361,8 @@ def mact_cube_error_lut(h, method, lut):
 # ------------------------------------------------ batched plans, autotuner
 
 def _image_array(images, outs):
+    if len(outs) != len(images):
+        raise ValueError("outs must hold one output per image")
     arr = (Image * max(len(images), 1))()
     for i, ((rgb, space), out) in enumerate(zip(images, outs)):
         arr[i] = _image(rgb, space, out)
@@ -418,7 +443,7 @@ def _planar(x):
 def mact_lab_forward(h, x, out=None, stream=None):
     """CIELAB of linear RGB x (N, 3, ...) -> same shape."""
     nb, hw = _planar(x)
-    out = torch.empty_like(x) if out is None else out
+    out = torch.empty_like(x) if out is None else _need(out, "out", x.shape)
     _check(lib().mact_lab_forward(h.ptr, _VP(x.data_ptr()), nb, hw, _VP(out.data_ptr()), _stream(stream)),
            "mact_lab_forward")
     return out
@@ -427,8 +452,10 @@ def mact_lab_forward(h, x, out=None, stream=None):
 def mact_lab_backward(h, x, grad_lab, out=None, stream=None):
     """Vector-Jacobian product J(x)^T grad_lab."""
     nb, hw = _planar(x)
-    grad_lab = grad_lab.contiguous()
-    out = torch.empty_like(x) if out is None else out
+    if not isinstance(grad_lab, torch.Tensor):
+        raise TypeError("grad_lab must be a torch.Tensor")
+    grad_lab = _need(grad_lab.contiguous(), "grad_lab", x.shape)
+    out = torch.empty_like(x) if out is None else _need(out, "out", x.shape)
     _check(lib().mact_lab_backward(h.ptr, _VP(x.data_ptr()), _VP(grad_lab.data_ptr()), nb, hw,
                                    _VP(out.data_ptr()), _stream(stream)), "mact_lab_backward")
     return out
@@ -437,10 +464,9 @@ def mact_lab_backward(h, x, grad_lab, out=None, stream=None):
 def mact_lab_delta_e_loss(h, x, target_lab, grad=True, loss=None, grad_out=None, stream=None):
     """(mean Delta E*ab of Lab(x) vs target_lab as a 0-d tensor, dLoss/dx or None)."""
     nb, hw = _planar(x)
-    if target_lab.shape != x.shape or not target_lab.is_contiguous():
-        raise ValueError("target_lab must be contiguous with the shape of x")
-    loss = torch.empty((), dtype=torch.float32, device=x.device) if loss is None else loss
-    g = (torch.empty_like(x) if grad_out is None else grad_out) if grad else None
+    _need(target_lab, "target_lab", x.shape)
+    loss = torch.empty((), dtype=torch.float32, device=x.device) if loss is None else _need(loss, "loss", ())
+    g = (torch.empty_like(x) if grad_out is None else _need(grad_out, "grad_out", x.shape)) if grad else None
     _check(lib().mact_lab_delta_e_loss(h.ptr, _VP(x.data_ptr()), _VP(target_lab.data_ptr()), nb, hw,
                                        _VP(loss.data_ptr()), _VP(g.data_ptr() if g is not None else 0),
                                        _stream(stream)), "mact_lab_delta_e_loss")
@@ -537,9 +563,11 @@ def mact_serve_destroy(srv, timeout_ms=60000.0):
 
 def mact_lut_cache_build(h, lut, out=None, stream=None):
     """Caching layout of an (n, n, n, 3) FP32 LUT: ((n-1)^3, 8, 4) float32."""
-    n = lut.shape[0]
+    n = lut.shape[0] if isinstance(lut, torch.Tensor) and lut.dim() == 4 else 0
+    _need(lut, "lut", (n, n, n, 3))
     if out is None:
         out = torch.empty(((n - 1) ** 3, 8, 4), dtype=torch.float32, device=lut.device)
+    _need(out, "out", ((n - 1) ** 3, 8, 4))
     _check(lib().mact_lut_cache_build(h.ptr, _VP(lut.data_ptr()), n, _VP(out.data_ptr()), _stream(stream)),
            "mact_lut_cache_build")
     return out
@@ -549,10 +577,12 @@ def mact_lut_interp_cached(h, method, cache, n, rgb, out=None, sel=False, stream
     """As mact_lut_interp, from the caching layout of an n^3 LUT."""
     if rgb.dtype != torch.uint8 or not rgb.is_contiguous() or rgb.shape[-1] != 3:
         raise ValueError("rgb must be a contiguous (..., 3) uint8 tensor")
+    _need(cache, "cache", ((n - 1) ** 3, 8, 4))
     npix = rgb.numel() // 3
     if out is None:
         out = torch.empty((3, npix), dtype=torch.float32, device=rgb.device,
                           pin_memory=rgb.device.type == "cpu")
+    _need(out, "out", (3, npix))
     ptrs = (_VP * 3)(*(out[c].data_ptr() for c in range(3)))
     s = (torch.empty(npix, dtype=torch.int32, device=rgb.device, pin_memory=rgb.device.type == "cpu")
          if sel else None)
@@ -568,6 +598,7 @@ def mact_lut_build_hsi(h, n, out=None, device="cuda", stream=None):
     nodes (gray nodes: (0, 0, 0, I))."""
     if out is None:
         out = torch.empty((n, n, n, 4), dtype=torch.float32, device=device)
+    _need(out, "out", (n, n, n, 4))
     _check(lib().mact_lut_build_hsi(h.ptr, n, _VP(out.data_ptr()), _stream(stream)), "mact_lut_build_hsi")
     return out
 
@@ -579,10 +610,14 @@ def mact_lut_interp_hsi(h, lut4, rgb, out=None, stream=None):
         raise ValueError("lut4 must be a contiguous (n, n, n, 4) float32 tensor")
     if rgb.dtype != torch.uint8 or not rgb.is_contiguous() or rgb.shape[-1] != 3:
         raise ValueError("rgb must be a contiguous (..., 3) uint8 tensor")
+    n = lut4.shape[0]
+    if lut4.shape[1] != n or lut4.shape[2] != n:
+        raise ValueError("lut4 must be a cube (n, n, n, 4)")
     npix = rgb.numel() // 3
     if out is None:
         out = torch.empty((3, npix), dtype=torch.float32, device=rgb.device,
                           pin_memory=rgb.device.type == "cpu")
+    _need(out, "out", (3, npix))
     ptrs = (_VP * 3)(*(out[c].data_ptr() for c in range(3)))
     _check(lib().mact_lut_interp_hsi(h.ptr, _VP(lut4.data_ptr()), lut4.shape[0], _VP(rgb.data_ptr()), npix, ptrs,
                                      _stream(stream)), "mact_lut_interp_hsi")
