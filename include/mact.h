@@ -147,7 +147,9 @@ void mact_config_default(mact_config *cfg);
 mact_status mact_create(const mact_config *cfg, mact_handle *out);
 
 /* Free the handle's device block.  Work already enqueued with the handle must
- * have completed (the call synchronises the device before freeing). */
+ * have completed (the call synchronises the device before freeing).  Servers
+ * and batch plans created from h keep using it: destroy them first (the
+ * handle does not track them, so freeing it under them is undefined). */
 mact_status mact_destroy(mact_handle h);
 
 /* Convert one image to img->space (Sections "CIELAB Color Space", "HSI

@@ -91,6 +91,8 @@ static mact_status inval(const char *msg)
 
 // ---- configuration ---------------------------------------------------------
 
+static void build_gamma(const mact_rgb_def &d, float *g32, double *g64);
+
 static mact_status build_coeffs(const mact_config &cfg, Coeffs &co)
 {
     std::memset(&co, 0, sizeof(co));
@@ -110,6 +112,16 @@ static mact_status build_coeffs(const mact_config &cfg, Coeffs &co)
     if (!(d.gamma_slope > 0.0) || !(d.gamma_exponent > 0.0) || !(d.gamma_offset > -1.0) ||
         !std::isfinite(d.gamma_threshold))
         return inval("invalid gamma parameters");
+    {
+        // the linearised codes must be finite, non-decreasing and within
+        // [0, 1]: above 1, white leaves the cube-root fits' domain
+        float g32[256];
+        double g64[256];
+        build_gamma(d, g32, g64);
+        for (int v = 0; v < 256; ++v)
+            if (!std::isfinite(g64[v]) || g64[v] < 0.0 || g64[v] > 1.0 + 1e-6 || (v > 0 && g64[v] < g64[v - 1]))
+                return inval("gamma parameters give a linearised code outside [0, 1] or a decreasing curve");
+    }
 
     // cube root
     if (cfg.lab_coeffs != 0 && cfg.lab_coeffs != 1) return inval("lab_coeffs must be 0 or 1");

@@ -57,6 +57,28 @@ def test_create_rejects_bad_config_before_touching_the_gpu(L, field, value):
     assert L.mact_last_error()
 
 
+@pytest.mark.parametrize("fields", [
+    dict(gamma_offset=-0.5),                           # negative base of the power: NaN codes
+    dict(gamma_slope=0.01),                            # the linear toe climbs above 1
+    dict(gamma_threshold=0.5, gamma_slope=0.6),        # the toe ends above the power segment: not monotone
+    dict(gamma_exponent=1.0, gamma_offset=0.0, gamma_threshold=-1.0, gamma_slope=1.0)])
+def test_create_rejects_gamma_curves_outside_the_unit_interval(L, fields):
+    """Eq. equ_rgb_lin with user parameters must give finite, non-decreasing
+    linear codes in [0, 1]; the check runs on the host before any CUDA call.
+    The last case is the identity curve, which is accepted."""
+    from paper_1009_0854_gb300 import mact
+    cfg = mact.mact_config_default(**fields)
+    h = ctypes.c_void_p()
+    st = L.mact_create(ctypes.byref(cfg), ctypes.byref(h))
+    if fields.get("gamma_exponent") == 1.0:
+        assert st in (0, -3)              # valid: fails only at the device without a GPU
+        if st == 0:
+            L.mact_destroy(h)
+    else:
+        assert st == -1 and h.value is None
+        assert b"gamma" in L.mact_last_error()
+
+
 def test_create_rejects_white_above_reference(L):
     from paper_1009_0854_gb300 import mact
     cfg = mact.mact_config_default(white=[0.9, 1.0, 1.089058])
