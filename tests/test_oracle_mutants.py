@@ -77,6 +77,25 @@ MUTANTS = [
      "grad[b * 3 * hw + j * hw + i] = d->m[j] * gt[0] + d->m[3 + j] * gt[1] + d->m[6 + j] * gt[2];",
      "grad[b * 3 * hw + j * hw + i] = d->m[3 * j] * gt[0] + d->m[3 * j + 1] * gt[1] + d->m[3 * j + 2] * gt[2];"),
     ("grad_linear_slope", "        *df = 7.787;\n", "        *df = 7.787 * t;\n"),
+    # shared pieces and the cube statistics
+    ("poly_power_shift", "        s += a[i] * xp;\n        xp *= x;", "        xp *= x;\n        s += a[i] * xp;"),
+    ("gamma_exponent_inverted", "return pow((kp + d->offset) / (1.0 + d->offset), d->exponent);",
+     "return pow((kp + d->offset) / (1.0 + d->offset), 1.0 / d->exponent);"),
+    ("hue_case1_base", "if (r > b && g > b) return ORC_PI / 3.0 + orc_atan_sqrt3(",
+     "if (r > b && g > b) return ORC_PI / 6.0 + orc_atan_sqrt3("),
+    ("hue_case3_base", "if (b > g) return 5.0 * ORC_PI / 3.0 + orc_atan_sqrt3(",
+     "if (b > g) return 4.0 * ORC_PI / 3.0 + orc_atan_sqrt3("),
+    ("hue_arccos_reflection", "if (b > g) h = 2.0 * ORC_PI - h;", "if (b < g) h = 2.0 * ORC_PI - h;"),
+    ("sct_branch_threshold", "} else if (x >= 0.5) {", "} else if (x >= 0.6) {"),
+    ("sct_r_zero_angle", "B = ORC_PI / 2.0;                         /* R = 0, G > 0 */",
+     "B = 0.0;                                  /* R = 0, G > 0 */"),
+    ("hsi_lut_weight_axis", "(((c >> 1) & 1) ? f[1] : 1.0 - f[1])", "(((c >> 1) & 1) ? f[2] : 1.0 - f[1])"),
+    ("eps_cielab_compares_itself",
+     "orc_cielab_pixel(d, 0, NULL, 0, NULL, 0, r, g, b, e);\n                orc_cielab_pixel(d, 1, p, n, q, m, r, g, b, a);",
+     "orc_cielab_pixel(d, 1, p, n, q, m, r, g, b, e);\n                orc_cielab_pixel(d, 1, p, n, q, m, r, g, b, a);"),
+    ("eps_sct_inverse_channels", "orc_cielab_pixel(d, 0, NULL, 0, NULL, 0, back[0], back[1], back[2], a);",
+     "orc_cielab_pixel(d, 0, NULL, 0, NULL, 0, back[0], back[2], back[1], a);"),
+    ("cbrt_probs_channel", "c2 += t[2] > 0.008856;", "c2 += t[1] > 0.008856;"),
 ]
 
 TWO_PI = 2.0 * math.pi
