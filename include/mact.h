@@ -446,6 +446,29 @@ mact_status mact_lut_interp_hsi(mact_handle h, const float *d_lut4, int32_t n, c
  * before mact_create forces 0.  MACT_E_INVAL for a NULL handle. */
 int32_t mact_host_memory_access(mact_handle h);
 
+/* ---- host-side minimax fits (no device work, no handle) -----------------
+ * The coefficient fits mact_create performs on the host, for inspection and
+ * for callers that cache them.  Both are Remez exchanges written for this
+ * library; the results equioscillate at n + m + 2 (rational) or n + 2
+ * (polynomial) points. */
+
+/* Minimax rational p_n/q_m of t^(1/3) on [0.008856, 1] (Section
+ * "Approximation of the Cube-Root Function"; the form of Table
+ * tab_cbrt_rat, any degrees 1 <= n, m <= 6), normalised to q(0) = 1: what
+ * mact_config.lab_coeffs = 1 evaluates.  p and q (7 doubles each, caller
+ * owned) receive the ascending coefficients, zero-padded; *max_err (may be
+ * NULL) the levelled maximum absolute error.  MACT_E_INVAL for other degrees
+ * or NULL p or q; MACT_E_UNSUPPORTED if the exchange does not converge. */
+mact_status mact_fit_cbrt_rational(int32_t n, int32_t m, double *p, double *q, double *max_err);
+
+/* Minimax polynomial P_n of arctan(sqrt(3) x) on [0, 1] (Section
+ * "Approximation of the Inverse Tangent Function", the degrees 2..5 of
+ * Table tab_arctan): the HSI set of mact_config.hsi_coeffs = 0.  c (6
+ * doubles, caller owned) receives the ascending coefficients, zero-padded;
+ * *max_err (may be NULL) the levelled maximum absolute error.  MACT_E_INVAL
+ * for other degrees or NULL c; MACT_E_UNSUPPORTED if the exchange fails. */
+mact_status mact_fit_hsi_arctan(int32_t n, double *c, double *max_err);
+
 /* Message for a status code (static storage). */
 const char *mact_strerror(mact_status st);
 

@@ -691,6 +691,32 @@ int32_t mact_host_memory_access(mact_handle h)
     return h->any_host ? 1 : 0;
 }
 
+mact_status mact_fit_cbrt_rational(int32_t n, int32_t m, double *p, double *q, double *max_err)
+{
+    if (!p || !q) return inval("mact_fit_cbrt_rational: NULL p or q");
+    if (n < 1 || n > 6 || m < 1 || m > 6) return inval("mact_fit_cbrt_rational: degrees must be 1..6");
+    double e = 0.0;
+    if (!cbrt_rational_fit(n, m, p, q, &e)) {
+        set_error("Remez exchange for the cube-root rational did not converge");
+        return MACT_E_UNSUPPORTED;
+    }
+    if (max_err) *max_err = e;
+    return MACT_OK;
+}
+
+mact_status mact_fit_hsi_arctan(int32_t n, double *c, double *max_err)
+{
+    if (!c) return inval("mact_fit_hsi_arctan: NULL c");
+    if (n < 2 || n > 5) return inval("mact_fit_hsi_arctan: degree must be 2..5");
+    double e = 0.0;
+    if (!hsi_unit_interval_fit(n, c, &e)) {
+        set_error("Remez fit of arctan(sqrt(3)x) failed");
+        return MACT_E_UNSUPPORTED;
+    }
+    if (max_err) *max_err = e;
+    return MACT_OK;
+}
+
 const char *mact_strerror(mact_status st)
 {
     switch (st) {

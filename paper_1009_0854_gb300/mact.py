@@ -150,6 +150,12 @@ def lib():
         L.mact_lut_build_hsi.restype = ctypes.c_int
         L.mact_lut_interp_hsi.argtypes = [_VP, _VP, ctypes.c_int32, _VP, ctypes.c_int64, ctypes.POINTER(_VP), _VP]
         L.mact_lut_interp_hsi.restype = ctypes.c_int
+        L.mact_fit_cbrt_rational.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.mact_fit_cbrt_rational.restype = ctypes.c_int
+        L.mact_fit_hsi_arctan.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]
+        L.mact_fit_hsi_arctan.restype = ctypes.c_int
         L.mact_host_memory_access.argtypes = [_VP]
         L.mact_host_memory_access.restype = ctypes.c_int32
         for name in ("mact_create", "mact_destroy", "mact_convert", "mact_convert_batch", "mact_convert_batch_static",
@@ -632,6 +638,22 @@ def mact_host_memory_access(h):
     if r < 0:
         _check(r, "mact_host_memory_access")
     return r
+
+
+def mact_fit_cbrt_rational(n, m):
+    """The library's host-side minimax rational of t^(1/3) on [0.008856, 1]:
+    (p, q, max_err), ascending coefficients with q[0] = 1."""
+    p, q, e = (ctypes.c_double * 7)(), (ctypes.c_double * 7)(), ctypes.c_double()
+    _check(lib().mact_fit_cbrt_rational(int(n), int(m), p, q, ctypes.byref(e)), "mact_fit_cbrt_rational")
+    return list(p)[: n + 1], list(q)[: m + 1], e.value
+
+
+def mact_fit_hsi_arctan(n):
+    """The library's host-side minimax polynomial of arctan(sqrt(3) x) on
+    [0, 1]: (c, max_err), ascending coefficients."""
+    c, e = (ctypes.c_double * 6)(), ctypes.c_double()
+    _check(lib().mact_fit_hsi_arctan(int(n), c, ctypes.byref(e)), "mact_fit_hsi_arctan")
+    return list(c)[: n + 1], e.value
 
 
 def mact_strerror(status):
