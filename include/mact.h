@@ -263,8 +263,9 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
  * the backward differentiates exactly what the forward evaluates, including
  * the linear segment (slope 7.787) for t <= 0.008856.  Handles using the
  * cube-root polynomials (lab_m = 0) return MACT_E_UNSUPPORTED.  At most
- * 2^32 - 1 pixels per call.  Fastest when hw % 4 == 0 and every pointer is
- * 16-byte aligned. */
+ * 2^31 pixels (nbatch * hw) per call; larger calls give MACT_E_INVAL before
+ * any launch.  Fastest when hw % 4 == 0 and every pointer is 16-byte
+ * aligned. */
 
 /* d_lab (nbatch, 3, hw) = CIELAB of d_x. */
 mact_status mact_lab_forward(mact_handle h, const float *d_x, int64_t nbatch, int64_t hw, float *d_lab,

@@ -514,13 +514,18 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
 
 static mact_status check_grad(mact_handle h, int64_t nbatch, int64_t hw, const char *who)
 {
+    // sizes first (they need no handle): the kernels walk 32-bit grid-stride
+    // loops, and with at most 2^31 items index + stride stays below 2^32 and
+    // cannot wrap; the factors are bounded before the product, so it cannot
+    // overflow either
+    if (nbatch < 0 || hw < 0) return inval("negative size");
+    const int64_t kMax = int64_t(1) << 31;
+    if (nbatch > kMax || hw > kMax || nbatch * hw > kMax) return inval("more than 2^31 pixels");
     if (!h) return inval(who);
     if (h->cfg.exact == 0 && h->co.lab_rational == 0) {
         set_error("gradients are provided for the rational cube-root approximants and the exact form");
         return MACT_E_UNSUPPORTED;
     }
-    if (nbatch < 0 || hw < 0) return inval("negative size");
-    if (nbatch * hw >= (int64_t(1) << 32)) return inval("more than 2^32 - 1 pixels");
     return MACT_OK;
 }
 

@@ -83,9 +83,9 @@ __device__ __forceinline__ void back(const PixelLab &p, float gL, float ga, floa
 }
 
 // Work split: quads of 4 consecutive pixels of one image plane when
-// hw % 4 == 0, the pointers are 16-byte aligned and there are fewer than 2^32
-// quads (index math in 32 bits, 16-byte loads and stores); single pixels
-// otherwise.
+// hw % 4 == 0 and the pointers are 16-byte aligned (16-byte loads and
+// stores); single pixels otherwise.  Index math is 32-bit: the entry points
+// admit at most 2^31 pixels, so a grid-stride index never wraps.
 struct Geometry {
     int64_t hw;
     uint32_t per_img;     // work items per image (quads or pixels)

@@ -137,3 +137,24 @@ def test_newest_entry_points_reject_null(L):
     assert L.mact_host_memory_access(None) == -1
     assert L.mact_serve_set_mode(None, 0) == -1
     assert L.mact_lut_build_hsi(None, 17, None, None) == -1
+
+
+@pytest.mark.parametrize("nb,hw", [(1, (1 << 31) + 1), ((1 << 31) + 1, 1), (1 << 16, 1 << 16), (1 << 40, 1 << 40),
+                                   (-1, 4), (4, -1)])
+def test_gradient_sizes_refused_before_the_handle(L, nb, hw):
+    """The gradient entry points admit at most 2^31 pixels (their kernels use
+    32-bit grid-stride indices, which must not wrap); oversized or negative
+    calls are refused on the host before anything else, products included."""
+    calls = [lambda: L.mact_lab_forward(None, None, nb, hw, None, None),
+             lambda: L.mact_lab_backward(None, None, None, nb, hw, None, None),
+             lambda: L.mact_lab_delta_e_loss(None, None, None, nb, hw, None, None, None)]
+    for call in calls:
+        assert call() == -1
+        msg = L.mact_last_error()
+        assert b"2^31" in msg or b"negative" in msg, msg
+
+
+def test_gradient_size_limit_is_inclusive(L):
+    """Exactly 2^31 pixels passes the size check (then fails on the NULL handle)."""
+    assert L.mact_lab_forward(None, None, 2, 1 << 30, None, None) == -1
+    assert b"NULL handle" in L.mact_last_error()
