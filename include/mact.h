@@ -121,11 +121,16 @@ typedef struct {
 
 /* One image.  rgb: pointer (device, or host memory the device addresses) to
  * height rows of width interleaved pixels, rows pitch_bytes apart
- * (>= 3*width).  out[c]: pointers of the same kind to the three output planes, rows out_pitch_elems elements apart (>= width),
- * element type given by dtype.  space: mact_space; dtype: mact_dtype.
- * Fastest when rgb is 16-byte aligned, pitch_bytes == 3*width,
- * out_pitch_elems == width and every out[c] is 16-byte aligned; any other
- * layout is accepted and handled by a slower tail path. */
+ * (>= 3*width; any byte alignment).  out[c]: pointers of the same kind to
+ * the three output planes, rows out_pitch_elems elements apart (>= width),
+ * element type given by dtype; each must be aligned to its element size
+ * (4 bytes FP32, 2 bytes FP16), else MACT_E_INVAL before any launch.
+ * space: mact_space; dtype: mact_dtype.  width or height 0 is an empty
+ * image; at most 2^42 pixels.  Fastest when rgb is 16-byte aligned,
+ * pitch_bytes == 3*width, out_pitch_elems == width and every out[c] is
+ * 16-byte aligned; planes aligned only to their element size (three
+ * adjacent planes of an odd pixel count) take a shared-memory transpose
+ * path, and every other layout a guarded path, all with identical values. */
 typedef struct {
     const uint8_t *rgb;
     int64_t width, height, pitch_bytes;
@@ -140,10 +145,12 @@ typedef struct {
 void mact_config_default(mact_config *cfg);
 
 /* Validate *cfg and build a handle on the current device.  Rejects unknown
- * degrees and any RGB definition for which white maps to t > 1 + 1e-6 or a
+ * degrees, any RGB definition for which white maps to t > 1 + 1e-6 or a
  * non-positive white component (the cube-root approximants are fitted on
- * [0.008856, 1], Figure fig_cbrt).  Allocates about 4 KB of device memory.
- * *out is written only on success. */
+ * [0.008856, 1], Figure fig_cbrt), and gamma parameters whose linearised
+ * codes are not finite, non-decreasing and within [0, 1].  These checks run
+ * on the host before any CUDA call (MACT_E_INVAL).  Allocates about 4 KB of
+ * device memory.  *out is written only on success. */
 mact_status mact_create(const mact_config *cfg, mact_handle *out);
 
 /* Free the handle's device block.  Work already enqueued with the handle must
@@ -238,7 +245,9 @@ mact_status mact_convert_batch_static(mact_handle h, const mact_image *imgs, int
 
 /* Packing step of the LUT methods: fill d_lut (n^3 x 3 FP32, layout
  * d_lut[((i*n + j)*n + k)*3 + c], R outermost) with the exact CIELAB of the
- * node codes 255*(i,j,k)/(n-1), computed in FP32 with cbrtf.  2 <= n <= 64. */
+ * node codes 255*(i,j,k)/(n-1), computed in FP64 (cbrt) on the device and
+ * rounded once to FP32.  2 <= n <= 64; d_lut 4-byte aligned, else
+ * MACT_E_INVAL. */
 mact_status mact_lut_build(mact_handle h, int32_t n, float *d_lut, mact_stream stream);
 
 /* Extraction + interpolation (Section "Comparison with 3D Lookup Table
