@@ -158,3 +158,19 @@ def test_gradient_size_limit_is_inclusive(L):
     """Exactly 2^31 pixels passes the size check (then fails on the NULL handle)."""
     assert L.mact_lab_forward(None, None, 2, 1 << 30, None, None) == -1
     assert b"NULL handle" in L.mact_last_error()
+
+
+@pytest.mark.parametrize("fields", [
+    dict(gamma_threshold=0.04045, gamma_slope=12.92, gamma_offset=0.055, gamma_exponent=2.4),   # sRGB
+    dict(gamma_threshold=0.0, gamma_slope=1.0, gamma_offset=0.0, gamma_exponent=2.2),          # pure power
+    dict(gamma_threshold=2.0, gamma_slope=1.0, gamma_offset=0.0, gamma_exponent=1.0)])         # linear codes
+def test_create_accepts_common_gamma_curves(L, fields):
+    """Valid curves pass the host checks; without a GPU the call then fails
+    only at the device (MACT_E_CUDA)."""
+    from paper_1009_0854_gb300 import mact
+    cfg = mact.mact_config_default(**fields)
+    h = ctypes.c_void_p()
+    st = L.mact_create(ctypes.byref(cfg), ctypes.byref(h))
+    assert st in (0, -3), L.mact_last_error()
+    if st == 0:
+        L.mact_destroy(h)
