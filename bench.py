@@ -51,7 +51,7 @@ def peaks():
 
 
 KERNEL_FILES = {
-    "convert": ("common.cuh", "engine.cuh", "pixel.cuh", "k_convert.cu"),
+    "convert": ("common.cuh", "engine.cuh", "pixel.cuh", "convert_common.cuh", "k_convert.cu"),
     "lut": ("common.cuh", "engine.cuh", "k_lut.cu"),
 }
 
