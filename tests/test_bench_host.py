@@ -84,3 +84,26 @@ def test_serve_trace_is_deterministic():
     assert a == b
     assert all(0 < t < 0.5 for t, *_ in a)
     assert all(0.09e6 <= h * w <= 24.5e6 for _, h, w, _, _ in a)
+
+
+def test_clock_summary_reports_median_max_and_throttle_reasons():
+    """The clocks record of the bench line: median SM clock under load, the
+    maximum clock, and every throttle reason seen active in any sample
+    (hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap);
+    unreadable clock fields are skipped."""
+    cs = bench.ClockSampler(0)
+    na, act = "Not Active", "Active"
+    cs.rows = [
+        ["0", "2070", "2070", "900.1", "0x0", na, na, na, na],
+        ["0", "1965", "2070", "1400.0", "0x4", na, na, na, act],
+        ["0", "[N/A]", "2070", "1200.0", "0x0", na, na, na, na],
+        ["0", "2055", "2070", "1100.0", "0x8", act, na, na, na],
+    ]
+    s = cs.stop()
+    assert s["samples"] == 4
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_clock_summary_without_samples_is_none():
+    assert bench.ClockSampler(0).stop() is None
