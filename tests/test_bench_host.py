@@ -107,3 +107,20 @@ def test_clock_summary_reports_median_max_and_throttle_reasons():
 
 def test_clock_summary_without_samples_is_none():
     assert bench.ClockSampler(0).stop() is None
+
+
+def test_traffic_figures_only_for_unchanged_kernel_sources(tmp_path, monkeypatch):
+    """profiles/traffic.txt rows are reported only while the recorded hash of
+    their kernel sources matches the current one; comments are ignored."""
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        "# comment line\nmact_cielab 191098880 aaaa  # trailing comment\nlut33_trilinear 195258368 bbbb\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "source_hash", lambda g: {"convert": "aaaa", "lut": "cccc"}[g])
+    assert bench.traffic_table() == {"mact_cielab": 191098880.0}
+
+
+def test_committed_traffic_rows_name_known_kernel_groups():
+    rows = [l.split("#", 1)[0].split() for l in open(bench.os.path.join(bench.ROOT, "profiles", "traffic.txt"))]
+    rows = [r for r in rows if r]
+    assert rows and all(len(r) == 3 and bench.kernel_group(r[0]) in bench.KERNEL_FILES for r in rows)
