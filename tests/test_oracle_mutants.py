@@ -331,3 +331,56 @@ def test_planted_mistake_is_caught(mutant_libs, mid):
     with np.errstate(all="ignore"), _Using(mutant_libs[mid]):
         caught = first_failure()
     assert caught is not None, "no pin catches the planted mistake %s" % mid
+
+
+# ------------------------------------------- mistakes in the Python side
+
+def _cbrt44(mp, p=None, q=None):
+    eps, p0, q0 = O.tables.CBRT_RAT[(4, 4)]
+    rat = dict(O.tables.CBRT_RAT)
+    rat[(4, 4)] = (eps, p if p is not None else p0, q if q is not None else q0)
+    mp.setattr(O.tables, "CBRT_RAT", rat)
+
+
+def _sct(mp, name, n, fn):
+    tab = dict(getattr(O.tables, name))
+    eps, c = tab[n]
+    tab[n] = (eps, fn(list(c)))
+    mp.setattr(O.tables, name, tab)
+
+
+def _hsi_wrong_interval(mp):
+    mp.setattr(O.remez, "_HSI01", {})
+    mp.setattr(O.remez, "hsi_arctan_unit", lambda n: (
+        list(map(float, O.remez.remez_poly(lambda x: np.arctan(np.sqrt(3.0) * x), n, 0.0, 254.0 / 256.0)[0])), 0.0))
+
+
+PY_MUTANTS = [
+    # the paper's tables, transcribed in oracle/tables.py
+    ("table_cbrt44_digits_transposed",
+     lambda mp: _cbrt44(mp, q=[4.022100e-04, 5.414536e-02, 8.221562e-01, 1.800167, 3.513617e-01])),
+    ("table_cbrt44_numerator_denominator_swapped",
+     lambda mp: _cbrt44(mp, p=O.tables.CBRT_RAT[(4, 4)][2], q=O.tables.CBRT_RAT[(4, 4)][1])),
+    ("table_sct_f_a1_sign", lambda mp: _sct(mp, "SCT_F", 5, lambda c: c[:1] + [-c[1]] + c[2:])),
+    ("table_sct_arcsin_reversed", lambda mp: _sct(mp, "SCT_ARCSIN", 5, lambda c: c[::-1])),
+    ("table_sct_g_a2_scaled", lambda mp: _sct(mp, "SCT_G", 5, lambda c: c[:2] + [c[2] * 10.0] + c[3:])),
+    # the RGB definition (Eq. equ_rgb_lin, equ_rgb_xyz, the D65 white)
+    ("gamma_exponent_not_inverted", lambda mp: mp.setattr(O.tables, "BT709_GAMMA",
+                                                          dict(O.tables.BT709_GAMMA, exponent=0.45))),
+    ("white_point_digit", lambda mp: mp.setattr(O.tables, "D65_WHITE", [0.950456, 1.0, 1.088058])),
+    ("matrix_rows_swapped", lambda mp: mp.setattr(O.tables, "BT709_MATRIX",
+                                                  O.tables.BT709_MATRIX[6:] + O.tables.BT709_MATRIX[3:6] +
+                                                  O.tables.BT709_MATRIX[:3])),
+    # the HSI set: a fit on the printed rows' interval instead of [0, 1]
+    ("hsi_fit_on_printed_interval", _hsi_wrong_interval),
+]
+
+
+@pytest.mark.parametrize("mid", [m[0] for m in PY_MUTANTS])
+def test_planted_python_mistake_is_caught(monkeypatch, mid):
+    patch = dict(PY_MUTANTS)[mid]
+    with monkeypatch.context() as mp:
+        patch(mp)
+        with np.errstate(all="ignore"):
+            caught = first_failure()
+    assert caught is not None, "no pin catches the planted mistake %s" % mid
