@@ -278,7 +278,7 @@ def run_gpu(args):
                "ms_per_step": round(ems, 4)}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the host baseline is a 1-GPU figure
         cpu = cpu_baseline(args.cpu_pixels)
 
     if rank == 0:
