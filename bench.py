@@ -12,6 +12,16 @@ roofline fraction are reported under "rows" and "roofline_mact_cielab".
 Inputs rotate over 8 distinct copies of the cube (400 MB > the 129 MB L2),
 so no row reads its input from L2.
 
+The same line (one GPU only) also carries the metric's other halves:
+  large  -- MACT CIELAB (4,4) on one 16384 x 16384 image, FP32 and FP16
+            planes: Gpix/s and fraction of the measured HBM bandwidth;
+  served -- a seeded Poisson trace (2000 requests/s of 0.1-24 Mpx images,
+            --served-seconds long) through the continuous-batching server
+            (direct mode, MACT (4,4) and the fitted (6,6) rational) and
+            through the plain per-image exact-libm path, in the same process:
+            p50/p99/max latency and Gpix/s of each, with the max Delta E*ab of
+            each transform over the cube.
+
 --impl reference times the FP64 CPU oracle (the deliberately slow reference
 arm) on a bounded sample of the same workload.
 """
@@ -281,6 +291,24 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the host baseline is a 1-GPU figure
         cpu = cpu_baseline(args.cpu_pixels)
 
+    # the metric's other halves, on one GPU: MACT CIELAB on a single large
+    # image (the HBM-roofline row), and the serving trace (served p50/p99
+    # against the plain per-image exact path, with each path's max Delta E)
+    large = served = clk_more = None
+    if rank == 0 and world == 1 and not (args.no_large and args.no_served):
+        del outs, inputs
+        if e2e is not None:
+            del pin_out
+        torch.cuda.empty_cache()
+        more = ClockSampler(local)
+        more.start()
+        if not args.no_large:
+            large = large_headline(args.steps)
+        if not args.no_served:
+            served = serve_experiment(args.served_seconds, paths=("direct", "direct_fitted66", "plain"),
+                                      ring_bytes=4 << 30, budget=16 << 30)
+        clk_more = more.stop()
+
     if rank == 0:
         value = world * len(ROWS) * PIX / (ms / args.steps * 1e-3) / 1e9
         line = {
@@ -299,6 +327,9 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": launches,
+            "large": large,
+            "served": served,
+            "clocks_large_and_served": clk_more,
         }
         print(json.dumps(line))
     if world > 1:
@@ -392,6 +423,49 @@ def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+def time_convert(torch, mact, h, rgb, space, out, k):
+    """Mean CUDA-event time (ms) of k back-to-back conversions after 3
+    untimed ones, on the current stream."""
+    fn = lambda: mact.mact_convert(h, rgb, space, out=out)      # noqa: E731
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    a, b = _events(torch)
+    a.record()
+    for _ in range(k):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / k
+
+
+def large_headline(steps):
+    """MACT RGB->CIELAB (4,4) on one 16384 x 16384 image (the 512 x 512 parity
+    generator's recipe: gradients above, uniform noise below), FP32 and FP16
+    planes: Gpix/s and fraction of the measured HBM bandwidth.  Input 805 MB,
+    output 3.2 / 1.6 GB: far larger than L2, so no flush is needed."""
+    import torch
+    from paper_1009_0854_gb300 import mact, synth
+    dev = torch.device("cuda", 0)
+    hbm, kind = peaks()
+    h = mact.mact_create()
+    side = 16384
+    npx = side * side
+    rgb = torch.from_numpy(synth.gradient_noise_image(side, side, seed=0)).to(dev)
+    rows = {}
+    for dt, dname, bpp in ((torch.float32, "f32", 15), (torch.float16, "f16", 9)):
+        out = torch.empty((3, side, side), dtype=dt, device=dev)
+        ms = time_convert(torch, mact, h, rgb, "cielab", out, max(10, steps))
+        rows[dname] = {"ms": round(ms, 4), "gpix_s": round(npx / ms / 1e6, 2), "bytes_per_px": bpp,
+                       "gb_s": round(npx * bpp / ms / 1e6, 1), "hbm_frac": round(npx * bpp / ms / 1e6 / hbm, 4),
+                       "peak_gbs": hbm, "peak_source": kind}
+        del out
+    del rgb
+    h.close()
+    torch.cuda.empty_cache()
+    return {"workload": "MACT CIELAB (4,4), one 16384x16384 uint8 image (gradients + noise)", "rows": rows}
+
+
 def run_large_workload(args):
     """Single large images: the 512x512 parity generator (smooth gradients
     over the upper half, uniform noise below) at 8192x8192 and 16384x16384,
@@ -411,18 +485,7 @@ def run_large_workload(args):
             out = torch.empty((3, side, side), dtype=dt, device=dev)
             for hname, h in (("mact", hm), ("exact", he), ("mact66", h66)):
                 for space in (("cielab",) if hname == "mact66" else ("cielab", "hsi", "sct")):
-                    fn = lambda: mact.mact_convert(h, rgb, space, out=out)      # noqa: E731
-                    for _ in range(3):
-                        fn()
-                    torch.cuda.synchronize()
-                    a, b = _events(torch)
-                    k = max(5, args.steps // 4)
-                    a.record()
-                    for _ in range(k):
-                        fn()
-                    b.record()
-                    torch.cuda.synchronize()
-                    ms = a.elapsed_time(b) / k
+                    ms = time_convert(torch, mact, h, rgb, space, out, max(5, args.steps // 4))
                     rows["%d_%s_%s_%s" % (side, hname, space, dname)] = {
                         "ms": round(ms, 4), "gpix_s": round(npx / ms / 1e6, 2),
                         "gb_s": round(npx * bpp / ms / 1e6, 1), "hbm_frac": round(npx * bpp / ms / 1e6 / hbm, 4)}
@@ -641,25 +704,26 @@ class PinnedRing:
             self.live.popleft()
 
 
-def run_serve_workload(args):
+def serve_experiment(seconds, paths=("direct", "staged", "direct_fitted66", "plain"), ring_bytes=16 << 30,
+                     budget=16 << 30):
     """Poisson arrivals (2000/s) of 0.1-24 Mpx images, 50/25/25% CIELAB/HSI/SCT,
     pinned host input and output (outputs carved from one pinned ring shared by
-    every path), through the continuous-batching server (MACT, 16 GB staging
-    budget) in direct mode (the kernel reads and writes the pinned buffers in
-    place) and in staged mode (copies through the arena), in direct mode with
-    the library's fitted (6,6) cube-root rational (max Delta E near the exact
-    path's), and through the plain path (one request at a time: H2D,
-    exact-libm kernel, D2H).  Every
-    path first serves an untimed 0.25 s warm-up trace.  Latency counts from
-    the trace's arrival time."""
+    every path), through the continuous-batching server (MACT, a device-memory
+    admission budget of ``budget`` bytes) in direct mode (the kernel reads and
+    writes the pinned buffers in place) and in staged mode (copies through the
+    arena), in direct mode with the library's fitted (6,6) cube-root rational
+    (max Delta E near the exact path's), and through the plain path (one
+    request at a time: H2D, exact-libm kernel, D2H).  ``paths`` picks which
+    run.  Every path first serves an untimed 0.25 s warm-up trace.  Latency
+    counts from the trace's arrival time.  Returns a dict of results."""
     import torch
     from paper_1009_0854_gb300 import mact, synth
     dev = torch.device("cuda", 0)
-    trace = synth.serve_trace(rate=2000.0, duration=args.serve_seconds, seed=0)
+    trace = synth.serve_trace(rate=2000.0, duration=seconds, seed=0)
     warm_trace = synth.serve_trace(rate=2000.0, duration=0.25, seed=1)
     maxpx = max(h * w for _, h, w, _, _ in trace + warm_trace)
     pool_in = torch.from_numpy(synth.request_image(4096, 6144, 2, 7).reshape(-1)).pin_memory()  # 75 MB
-    ring = PinnedRing(torch, 16 << 30)
+    ring = PinnedRing(torch, ring_bytes)
 
     def link_gbs(dst_views, src):
         """Copy-engine D2H bandwidth into the given pinned views (one copy each)."""
@@ -677,8 +741,9 @@ def run_serve_workload(args):
 
     cal_src = torch.empty(64 << 20, dtype=torch.float32, device=dev)      # 256 MB
     step = ring.buf.numel() // 16
-    ring_gbs = link_gbs([ring.buf[k * step: k * step + (64 << 20)] for k in range(16)], cal_src)
-    ring0_gbs = link_gbs([ring.buf[: 64 << 20]] * 16, cal_src)
+    ring_gbs = link_gbs([ring.buf[k * step: k * step + min(step, 64 << 20)] for k in range(16)], cal_src)
+    ring0_gbs = link_gbs([ring.buf[: min(step, 64 << 20)]] * 16, cal_src)
+    del cal_src
 
     def req_in(hgt, wid):
         return pool_in[: hgt * wid * 3].view(hgt, wid, 3)
@@ -698,7 +763,7 @@ def run_serve_workload(args):
     def served(tr, mode, hs=None):
         """The driver submits at each arrival time and, while waiting for the
         next one, retires every finished request (its ring slot is released)."""
-        srv = mact.mact_serve_create(hs or h, 16 << 30, max_slots=128)
+        srv = mact.mact_serve_create(hs or h, budget, max_slots=128)
         mact.mact_serve_set_mode(srv, mode)
         inflight = collections.OrderedDict()    # ticket -> (arrival, submit, ring entry)
         lat = []
@@ -763,7 +828,8 @@ def run_serve_workload(args):
                                                    "queue_p99_ms", "h2d_p99_ms", "compute_p99_ms", "d2h_p99_ms")}
         stages["d2h_busy_ms"] = round(st["d2h_busy_ms"], 1)
         stages["d2h_copy_gbs"] = round(st["d2h_copy_gbs"], 1)
-        return summary(lat, npx, wall, {"batches": st["batches"], "server_p50_ms": round(st["p50_ms"], 3),
+        return summary(lat, npx, wall, {"mode": mode, "budget_bytes": budget, "batches": st["batches"],
+                                        "server_p50_ms": round(st["p50_ms"], 3),
                                         "server_p99_ms": round(st["p99_ms"], 3), "server_stages_ms": stages,
                                         "client": stats})
 
@@ -793,10 +859,10 @@ def run_serve_workload(args):
             npx += hgt * wid
         return summary(lat, npx, time.perf_counter() - t0)
 
-    served(warm_trace, "direct")
-    served(warm_trace, "staged")
-    served(warm_trace, "direct", h66)
-    plain(warm_trace)
+    runners = {"direct": lambda tr: served(tr, "direct"), "staged": lambda tr: served(tr, "staged"),
+               "direct_fitted66": lambda tr: served(tr, "direct", h66), "plain": plain}
+    for p in paths:
+        runners[p](warm_trace)
 
     def same_delta_e():
         """Served results equal single-image conversions bit for bit (checked
@@ -817,17 +883,28 @@ def run_serve_workload(args):
         srv.close()
         e_mact = mact.mact_cube_error(h, "cielab")
         e_66 = mact.mact_cube_error(h66, "cielab")
-        e_exact = mact.mact_cube_error(mact.mact_create(exact=1), "cielab")
+        e_exact = mact.mact_cube_error(he, "cielab")
         return {"sampled_requests": k, "served_bit_identical_to_single_image": same,
                 "mact_cielab_delta_e_max_cube": round(e_mact[1], 6),
                 "mact_cielab_delta_e_avg_cube": round(e_mact[0], 6),
                 "fitted66_cielab_delta_e_max_cube": round(e_66[1], 8),
                 "fitted66_cielab_delta_e_avg_cube": round(e_66[0], 8),
                 "exact_fp32_cielab_delta_e_max_cube": round(e_exact[1], 8)}
-    results = {"served_direct": served(trace, "direct"), "served_staged": served(trace, "staged"),
-               "served_direct_fitted66": served(trace, "direct", h66),
-               "plain_exact_per_image": plain(trace), "same_delta_e": same_delta_e(),
-               "link": {"d2h_gbs_ring_spread": ring_gbs, "d2h_gbs_ring_start": ring0_gbs}}
+    names = {"direct": "served_direct", "staged": "served_staged", "direct_fitted66": "served_direct_fitted66",
+             "plain": "plain_exact_per_image"}
+    results = {names[p]: runners[p](trace) for p in paths}
+    results["same_delta_e"] = same_delta_e()
+    results["link"] = {"d2h_gbs_ring_spread": ring_gbs, "d2h_gbs_ring_start": ring0_gbs}
+    results["trace"] = {"rate_per_s": 2000.0, "seconds": seconds, "requests": len(trace),
+                        "offered_gpix_s": round(sum(hh * ww for _, hh, ww, _, _ in trace) / seconds / 1e9, 3)}
+    del ring, pool_in, dbuf_in, dbuf_out
+    torch.cuda.empty_cache()
+    return results
+
+
+def run_serve_workload(args):
+    """The serving trace through every path (see serve_experiment)."""
+    results = serve_experiment(args.serve_seconds)
     print(json.dumps({"workload": "serve: Poisson 2000 req/s for %g s, 0.1-24 Mpx, pinned host buffers"
                       % args.serve_seconds, "rows": results}))
 
@@ -845,7 +922,11 @@ def main():
     ap.add_argument("--workload", default="cube", choices=["cube", "batch", "serve", "grad", "lut", "large"],
                     help="cube: the default step; the others measure the batched, served and "
                          "differentiable forms on their own workloads")
-    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of --workload serve's trace")
+    ap.add_argument("--served-seconds", type=float, default=10.0,
+                    help="length of the serving trace in the default line's 'served' key")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
     if args.impl == "reference":

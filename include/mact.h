@@ -232,14 +232,19 @@ mact_status mact_get_batch_shape(mact_handle h, int32_t *threads, int32_t *px_pe
  * another framework's pool.  The work list (at most 1024 images; count above
  * that returns MACT_E_INVAL) and the tile counters live in a fixed array of
  * about 90 KB compiled into the library; every GPU that loads the library
- * keeps it until the process exits.  The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress) with the device
- * current, so make the first call on each device before any stream capture.
- * Every call shares the one array: calls whose work overlaps on the GPU
- * (different streams, or different handles, at the same time) race and must
- * be serialised by the caller.  Calls from several host threads are
- * serialised by the library.  Uploads the work list with cudaMemsetAsync and
- * cudaMemcpyAsync on stream, then launches the batched kernel. */
+ * keeps it until the process exits.  The first call on a device that uses
+ * the array looks up its device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture begins.
+ * The current device must be the handle's device, else MACT_E_INVAL.
+ * The launch shape is the handle's batch shape, as for mact_convert_batch.
+ * Lists of more than 32 non-empty images are written into the array by small
+ * upload kernels whose parameters carry the descriptors (no host buffer is
+ * read after the call returns), the first of which zeroes the tile counters;
+ * shorter lists go by value to the batched kernel and use no array at all.
+ * Every call shares the one array and it keeps the last call's contents:
+ * calls whose work overlaps on the GPU (different streams, or different
+ * handles, at the same time) race and must be serialised by the caller.
+ * Calls from several host threads are serialised by the library. */
 mact_status mact_convert_batch_static(mact_handle h, const mact_image *imgs, int32_t count,
                                       mact_stream stream);
 

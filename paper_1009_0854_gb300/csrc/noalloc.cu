@@ -14,6 +14,14 @@
 // library holds it until the process exits.  Host code cannot use the
 // symbol as a device address, so each device's address is looked up once
 // with cudaGetSymbolAddress (with that device current) and cached.
+//
+// The work list reaches the array without any host staging buffer: each
+// chunk of descriptors travels by value in the parameter block of a small
+// upload kernel (the launch copies the parameters when it is enqueued, so no
+// host memory is read after the call returns), and that kernel writes the
+// chunk into the array.  The first chunk also zeroes the tile counters.
+// Lists of at most kParamImages images skip the array altogether: they go by
+// value to the batched kernel itself, exactly as in mact_convert_batch.
 #include <mutex>
 
 #include "internal.h"
@@ -24,14 +32,33 @@ constexpr int32_t kStaticMaxImages = 1024;
 constexpr size_t kStaticCounterBytes = 256;
 constexpr size_t kStaticScratchBytes = kStaticCounterBytes + kStaticMaxImages * sizeof(ImageDesc);
 constexpr int kStaticMaxDevices = 64;
+// descriptors per upload launch: 256 x 88 B = 22.5 KB of kernel parameters
+// (within the 32,764-byte parameter limit of CUDA 12.1 and later)
+constexpr int32_t kStaticChunk = 256;
 
 static __device__ __align__(256) unsigned char g_batch_scratch[kStaticScratchBytes];
 
+struct StaticChunk {
+    ImageDesc img[kStaticChunk];
+};
+static_assert(sizeof(StaticChunk) + 16 <= 32764, "upload chunk exceeds the kernel parameter limit");
+static_assert(kStaticMaxImages % kStaticChunk == 0, "whole chunks");
+
+// Writes descriptors [first, first + n) of the work list; zero_ctr: also
+// reset the two tile counters (the array keeps the previous call's values).
+__global__ void __launch_bounds__(kStaticChunk)
+k_static_upload(const __grid_constant__ StaticChunk chunk, int32_t n, int32_t first, int32_t zero_ctr)
+{
+    ImageDesc *list = reinterpret_cast<ImageDesc *>(g_batch_scratch + kStaticCounterBytes);
+    const int i = threadIdx.x;
+    if (i < n) list[first + i] = chunk.img[i];
+    if (zero_ctr && i < 2) reinterpret_cast<unsigned long long *>(g_batch_scratch)[i] = 0ull;
+}
+
 namespace {
 
-std::mutex g_static_mu;                       // guards the tables below
+std::mutex g_static_mu;                       // guards the table below
 void *g_static_ptr[kStaticMaxDevices];        // device address of g_batch_scratch, per device
-ImageDesc g_static_host[kStaticMaxImages];    // host-side work list staging (static, not heap)
 
 // Device address of the scratch array on the current device (set-up on the
 // first call per device).  Called with g_static_mu held.
@@ -77,34 +104,69 @@ extern "C" mact_status mact_convert_batch_static(mact_handle h, const mact_image
         if (st == MACT_OK) st = check_image_access(*h, imgs[i]);
         if (st != MACT_OK) return st;
     }
-    cudaStream_t s = (cudaStream_t)stream;
-    std::lock_guard<std::mutex> lock(g_static_mu);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch_static: cudaGetDevice");
+    if (dev != h->device) {
+        // the handle's coefficient and gamma pointers belong to its own device
+        set_error("mact_convert_batch_static: the current device is not the handle's device");
+        return MACT_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    BatchCfg cfg;
+    {
+        std::lock_guard<std::mutex> lock(h->batch_mu);
+        cfg = h->batch_cfg;
+    }
+    int per_sm = batch_blocks_per_sm(*h, cfg);
+    if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
+
+    int32_t nonempty = 0;
+    for (int32_t i = 0; i < count; ++i) nonempty += (imgs[i].width != 0 && imgs[i].height != 0);
+    if (nonempty == 0) return MACT_OK;
+    if (nonempty <= kParamImages) {   // short list: by value to the batched kernel, no scratch
+        ParamList list{};
+        int64_t total = 0;
+        int32_t n = 0;
+        for (int32_t i = 0; i < count; ++i) {
+            if (imgs[i].width == 0 || imgs[i].height == 0) continue;
+            ImageDesc d = make_desc(imgs[i], cfg.tile_px());
+            d.tile_begin = total;
+            total += tiles_of(d);
+            list.img[n++] = d;
+        }
+        int64_t grid = (int64_t)h->num_sms * per_sm;
+        if (grid > total) grid = total;
+        return cuda_status(launch_batch_param(*h, list, n, total, (int)grid, s, cfg),
+                           "mact_convert_batch_static launch");
+    }
+
+    std::lock_guard<std::mutex> lock(g_static_mu);
     void *scratch = nullptr;
     mact_status st = static_scratch(dev, &scratch);
     if (st != MACT_OK) return st;
-
-    int64_t total = 0;
-    int32_t n = 0;
-    for (int32_t i = 0; i < count; ++i) {
-        if (imgs[i].width == 0 || imgs[i].height == 0) continue;
-        ImageDesc d = make_desc(imgs[i]);
-        d.tile_begin = total;
-        total += tiles_of(d);
-        g_static_host[n++] = d;
-    }
-    if (total == 0) return MACT_OK;
     unsigned long long *d_ctr = reinterpret_cast<unsigned long long *>(scratch);
     ImageDesc *d_imgs = reinterpret_cast<ImageDesc *>(static_cast<unsigned char *>(scratch) + kStaticCounterBytes);
-    // the array keeps the previous call's contents: the tile counters must
-    // start at zero.  The copy is from pageable host memory, so it has
-    // consumed g_static_host when cudaMemcpyAsync returns.
-    e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned long long), s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_imgs, g_static_host, n * sizeof(ImageDesc), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch_static: work list upload");
-    int64_t grid = (int64_t)h->num_sms * batch_blocks_per_sm(*h);
+
+    StaticChunk chunk;   // on the host stack; copied into each launch's parameters
+    int64_t total = 0;
+    int32_t n = 0, fill = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        if (imgs[i].width == 0 || imgs[i].height == 0) continue;
+        ImageDesc d = make_desc(imgs[i], cfg.tile_px());
+        d.tile_begin = total;
+        total += tiles_of(d);
+        chunk.img[fill++] = d;
+        ++n;
+        if (fill == kStaticChunk || n == nonempty) {
+            k_static_upload<<<1, kStaticChunk, 0, s>>>(chunk, fill, n - fill, n == fill ? 1 : 0);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_status(e, "mact_convert_batch_static: work list upload");
+            fill = 0;
+        }
+    }
+    int64_t grid = (int64_t)h->num_sms * per_sm;
     if (grid > total) grid = total;
-    return cuda_status(launch_batch(*h, d_imgs, n, total, d_ctr, (int)grid, s), "mact_convert_batch_static launch");
+    return cuda_status(launch_batch(*h, d_imgs, n, total, d_ctr, (int)grid, s, cfg),
+                       "mact_convert_batch_static launch");
 }

@@ -77,6 +77,91 @@ def test_vjp_matches_oracle_and_fused(hx):
     assert (g1 - g2).abs().max().item() <= 1e-4 * scale
 
 
+def _delta_e(h, x, tgt):
+    """Per-pixel Delta E*ab (FP64) of the FP32 GPU forward of x against tgt."""
+    lab = mact.mact_lab_forward(h, torch.from_numpy(np.ascontiguousarray(x)).cuda()).cpu().numpy()
+    return np.sqrt(((lab.astype(np.float64) - tgt) ** 2).sum(axis=1))
+
+
+def test_finite_differences_of_the_gpu_forward(hx):
+    """Finite differences of the per-pixel Delta E*ab that the FP32 GPU
+    forward computes, on 1536 pixels drawn like the gradient workload (5% gray
+    pixels at exactly 0 or within 1e-4 of the knee), against the FP64 oracle's
+    analytic gradient and against the GPU's own fused gradient, element by
+    element.
+
+    Away from the knee: central differences with step h = 1e-3.  Where some
+    channel's t lies within h |M| of the knee (t = M x, M the matrix rows over
+    the white point): the one-sided three-point difference, step 2e-4, on the
+    side that keeps every channel on its own branch (the quotient across the
+    knee is meaningless: the two branches meet with different slopes).
+
+    Tolerance: |FD - g| <= c e / s + r |g|.  e is the largest
+    |Delta E_gpu - Delta E_oracle| measured over every evaluated point (the
+    FP32 rounding noise), c / s the stencil's noise gain (2 / (2h) central,
+    8 / (2 * 2e-4) one-sided), and r the truncation allowance: 5e-3 central,
+    1e-2 one-sided (the FP64 oracle's own differences on these pixels stay
+    below 2.5e-3 and 5.4e-3)."""
+    h, exact = hx
+    x, tgt_rgb = synth.linear_rgb_batch(n=1, h=32, w=48, seed=7)
+    tgt = O.lab_linear(tgt_rgb).astype(np.float32).astype(np.float64)
+    P = x[0, 0].size
+    assert P >= 1000
+    _, g_orc = O.lab_loss_grad(x, tgt, exact=exact)
+    g_orc = g_orc * P                       # d Delta E / dx per pixel (loss = mean)
+    _, g_gpu = mact.mact_lab_delta_e_loss(h, torch.from_numpy(x).cuda(), torch.from_numpy(tgt.astype(np.float32)).cuda())
+    g_gpu = g_gpu.cpu().numpy().astype(np.float64) * P
+    M = np.array(tables.BT709_MATRIX).reshape(3, 3) / np.array(tables.D65_WHITE)[:, None]
+    t = np.einsum("cj,njp->ncp", M, x.reshape(1, 3, -1).astype(np.float64)).reshape(x.shape)
+    hc, hs = 1e-3, 2e-4
+    noise = [0.0]
+
+    def de(xx):
+        d = _delta_e(h, xx, tgt)
+        ref = np.sqrt(((O.lab_linear(xx.astype(np.float64), exact=exact) - tgt) ** 2).sum(axis=1))
+        noise[0] = max(noise[0], float(np.abs(d - ref).max()))
+        return d
+
+    def shifted(c, step):
+        y = x.copy()
+        y[:, c] = (y[:, c].astype(np.float64) + step).astype(np.float32)
+        return y
+
+    f0 = de(x)
+    checked = 0
+    for c in range(3):
+        col = M[:, c][None, :, None, None]
+        near = (np.abs(t - KNEE) <= hc * col).any(axis=1)
+        up_ok = ((t > KNEE) == (t + 2 * hs * col > KNEE)).all(axis=1)
+        dn_ok = ((t > KNEE) == (t - 2 * hs * col > KNEE)).all(axis=1)
+        ambiguous = (np.abs(t - KNEE) < 1e-6).any(axis=1) | (near & ~up_ok & ~dn_ok)
+        assert ambiguous.sum() <= 4
+        xp, xm = shifted(c, hc), shifted(c, -hc)
+        central = (de(xp) - de(xm)) / (xp[:, c].astype(np.float64) - xm[:, c])
+        # quadratic through (x0, f0), (x1, f1), (x2, f2), differentiated at x0
+        # (the exact spacing of the FP32 points)
+        sides = []
+        for sgn in (1, -1):
+            x1, x2 = shifted(c, sgn * hs), shifted(c, 2 * sgn * hs)
+            a0, a1, a2 = x[:, c].astype(np.float64), x1[:, c].astype(np.float64), x2[:, c].astype(np.float64)
+            f1, f2 = de(x1), de(x2)
+            sides.append(f0 * (2 * a0 - a1 - a2) / ((a0 - a1) * (a0 - a2)) +
+                         f1 * (a0 - a2) / ((a1 - a0) * (a1 - a2)) + f2 * (a0 - a1) / ((a2 - a0) * (a2 - a1)))
+        one_sided = np.where(up_ok, sides[0], sides[1])
+        fd = np.where(near, one_sided, central)
+        tol_noise = np.where(near, 8.0 / (2 * hs), 2.0 / (2 * hc))
+        tol_rel = np.where(near, 1e-2, 5e-3)
+        use = ~ambiguous
+        for what, g in (("oracle", g_orc[:, c]), ("gpu", g_gpu[:, c])):
+            tol = tol_noise * noise[0] + tol_rel * np.abs(g)
+            bad = use & (np.abs(fd - g) > tol)
+            assert not bad.any(), "%s channel %d: FD %r vs %r at %s" % (
+                what, c, fd[bad][:3], g[bad][:3], np.argwhere(bad)[:3].tolist())
+        checked += int(use.sum())
+    assert noise[0] <= np.sqrt(3) * LAB_TOL
+    assert checked >= 3 * 1500
+
+
 def test_autograd_gradcheck(hx):
     """torch.autograd.gradcheck of the Lab wrapper (FP32, central differences
     with eps = 1e-3) on inputs away from the knee."""

@@ -1,6 +1,7 @@
 """The served form: continuous batching with a memory budget.  Every result
 must equal the single-image conversion of the same image, whether the
-request ran alone or in a mix with others."""
+request ran alone or in a mix with others, and must match the FP64 oracle
+element by element within the parity tolerances of its space."""
 import time
 
 import numpy as np
@@ -8,6 +9,7 @@ import pytest
 import torch
 
 from paper_1009_0854_gb300 import mact, synth
+from parity import check_space, oracle_planes
 
 pytestmark = pytest.mark.gpu
 
@@ -34,15 +36,28 @@ def _reference(h, reqs):
     return refs
 
 
-def test_each_result_same_alone_and_in_the_mix(h):
+@pytest.fixture(scope="module")
+def mix_requests():
+    """48 uneven requests (FP32 and FP16 planes, all three spaces) with their
+    FP64 oracle planes."""
     reqs = _requests(3, 48)
+    return reqs, [oracle_planes(space, im) for im, space, _ in reqs]
+
+
+@pytest.mark.parametrize("mode", ["direct", "staged"])
+def test_each_result_same_alone_and_in_the_mix(h, mode, mix_requests):
+    """Alone and in the mix, in both serving modes: each result equals the
+    single-image conversion bit for bit and the oracle within tolerance."""
+    reqs, orc = mix_requests
     refs = _reference(h, reqs)
     srv = mact.mact_serve_create(h, 256 << 20, max_slots=16)
+    mact.mact_serve_set_mode(srv, mode)
     # alone: one request at a time
-    for (im, space, dt), ref in zip(reqs[:12], refs[:12]):
+    for (im, space, dt), ref, o in zip(reqs[:12], refs[:12], orc[:12]):
         t, out = mact.mact_serve_submit(srv, torch.from_numpy(im).pin_memory(), space, dtype=dt)
         mact.mact_serve_wait(srv, t, 30000)
         assert torch.equal(out, ref)
+        check_space(space, out, o, dtype=dt, what="served alone (%s) %s %s" % (mode, space, im.shape))
         mact.mact_serve_release(srv, t)
     # in the mix: everything at once, host (pinned), pageable and device buffers
     pending = []
@@ -55,9 +70,10 @@ def test_each_result_same_alone_and_in_the_mix(h):
             rgb = torch.from_numpy(im).cuda()
         t, out = mact.mact_serve_submit(srv, rgb, space, dtype=dt)
         pending.append((t, out, ref))
-    for t, out, ref in pending:
+    for (t, out, ref), (im, space, dt), o in zip(pending, reqs, orc):
         mact.mact_serve_wait(srv, t, 60000)
         assert torch.equal(out.cpu(), ref)
+        check_space(space, out, o, dtype=dt, what="served in the mix (%s) %s %s" % (mode, space, im.shape))
     st = mact.mact_serve_stats(srv)
     assert st["completed"] == 12 + 48 and st["failed"] == 0
     assert st["batches"] >= 2
