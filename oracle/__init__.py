@@ -64,6 +64,8 @@ def lib():
                                        ctypes.c_int] + [ctypes.c_double] * 3 + [_D]
         L.orc_cielab.argtypes = [ctypes.POINTER(RGBDef), ctypes.c_int, _D, ctypes.c_int, _D,
                                  ctypes.c_int, _U8, ctypes.c_int64, _D, _D, _D, ctypes.c_int]
+        L.orc_cieluv_pixel.argtypes = L.orc_cielab_pixel.argtypes
+        L.orc_cieluv.argtypes = L.orc_cielab.argtypes
         L.orc_hsi.argtypes = [ctypes.c_int, _D, ctypes.c_int, _U8, ctypes.c_int64, _D, _D, _D,
                               ctypes.c_int]
         L.orc_sct.argtypes = [ctypes.POINTER(SCTCoeffs), _U8, ctypes.c_int64, _D, _D, _D,
@@ -192,6 +194,22 @@ def cielab(rgb, exact=False, n=4, m=4, p=None, q=None, rgbdef=None, nthreads=0):
                      (len(q) - 1) if q is not None else -1,
                      _ptr(rgb, _U8), npix, _ptr(L, _D), _ptr(A, _D), _ptr(B, _D), nthreads)
     return [x.reshape(rgb.shape[:-1]) for x in (L, A, B)]
+
+
+def cieluv(rgb, exact=False, n=4, m=4, p=None, q=None, rgbdef=None, nthreads=0):
+    """RGB -> CIE 1976 L*u*v* (the CIELUV variant the Conclusions name): L* as
+    in CIELAB (the cube root exact or replaced by p/q, default Table
+    tab_cbrt_rat (4,4)), u* = 13 L* (u' - u'n), v* = 13 L* (v' - v'n)."""
+    rgb, npix = _rgb(rgb)
+    if p is None:
+        p, q = cbrt_coeffs(n, m)
+    d = rgbdef or bt709_d65()
+    pa, qa = _darr(p), _darr(q or [1.0])
+    (L, U, V), _ = _planes(npix, rgb.shape[:-1])
+    lib().orc_cieluv(ctypes.byref(d), 0 if exact else 1, pa, len(p) - 1, qa,
+                     (len(q) - 1) if q is not None else -1,
+                     _ptr(rgb, _U8), npix, _ptr(L, _D), _ptr(U, _D), _ptr(V, _D), nthreads)
+    return [x.reshape(rgb.shape[:-1]) for x in (L, U, V)]
 
 
 def hsi(rgb, mode="approx", n=5, printed=False, coeffs=None, nthreads=0):
@@ -323,6 +341,17 @@ def cube_eps_cielab(n=4, m=4, p=None, q=None, rgbdef=None):
     d = rgbdef or bt709_d65()
     out = (ctypes.c_double * 2)()
     lib().orc_cube_eps_cielab(ctypes.byref(d), _darr(p), len(p) - 1, _darr(q or [1.0]),
+                              (len(q) - 1) if q is not None else -1, out)
+    return list(out)
+
+
+def cube_eps_cieluv(n=4, m=4, p=None, q=None, rgbdef=None):
+    """(eps_avg, eps_max) in Delta E*uv of MACT CIELUV over all 2^24 colours."""
+    if p is None:
+        p, q = cbrt_coeffs(n, m)
+    d = rgbdef or bt709_d65()
+    out = (ctypes.c_double * 2)()
+    lib().orc_cube_eps_cieluv(ctypes.byref(d), _darr(p), len(p) - 1, _darr(q or [1.0]),
                               (len(q) - 1) if q is not None else -1, out)
     return list(out)
 

@@ -19,6 +19,9 @@
  *    gamma-encoded codes directly.
  *  - f(t) uses the approximant only for t > 0.008856 (Eq. equ_xyz_lab); the
  *    linear segment 7.787 t + 16/116 is kept exactly.  No clamp of t to 1.
+ *  - CIELUV (named in the Conclusions, defined by the CIE, not printed):
+ *    L* as in CIELAB, u* = 13 L* (u' - u'n), v* = 13 L* (v' - v'n); black
+ *    gives u* = v* = 0.
  *  - HSI hue: Kender's case chain (Eq. equ_rgb_kender) evaluated in the
  *    printed order with strict comparisons; hue 0 when max-min (chroma) is 0
  *    (the "undefined" case); S = 0 for black.
@@ -171,6 +174,77 @@ ORC_API double orc_delta_e(const double x[3], const double y[3])
 {
     double dl = x[0] - y[0], da = x[1] - y[1], db = x[2] - y[2];
     return sqrt(dl * dl + da * da + db * db);
+}
+
+/* ------------------------------------------------------------------ CIELUV */
+/* The paper's Conclusions note that the method carries over to CIELUV,
+ * whose only costly step is the same cube root in L*.  CIE 1976 L*u*v*
+ * (the standard definition, not printed in the paper):
+ *   L* = 116 f(Y/Yn) - 16, with f the Eq. equ_xyz_lab function (exact, or the
+ *        MACT approximant for t > 0.008856);
+ *   u' = 4X / (X + 15Y + 3Z), v' = 9Y / (X + 15Y + 3Z), and u'n, v'n the same
+ *        of the reference white;
+ *   u* = 13 L* (u' - u'n), v* = 13 L* (v' - v'n).
+ * Black (X + 15Y + 3Z = 0) has no chromaticity: u* = v* = 0 there.  XYZ are
+ * the un-normalised tristimulus values t_c * white_c. */
+ORC_API void orc_cieluv_pixel(const orc_rgbdef *d, int mode,
+                              const double *p, int n, const double *q, int m,
+                              double r, double g, double b, double luv[3])
+{
+    double t[3];
+    orc_rgb_to_t(d, r, g, b, t);
+    const double X = t[0] * d->white[0], Y = t[1] * d->white[1], Z = t[2] * d->white[2];
+    const double fy = mode ? orc_f_approx(t[1], p, n, q, m) : orc_f_exact(t[1]);
+    const double L = 116.0 * fy - 16.0;
+    const double Xn = d->white[0], Yn = d->white[1], Zn = d->white[2];
+    const double dn = Xn + 15.0 * Yn + 3.0 * Zn;
+    const double un = 4.0 * Xn / dn, vn = 9.0 * Yn / dn;
+    const double den = X + 15.0 * Y + 3.0 * Z;
+    luv[0] = L;
+    if (den > 0.0) {
+        luv[1] = 13.0 * L * (4.0 * X / den - un);
+        luv[2] = 13.0 * L * (9.0 * Y / den - vn);
+    } else {
+        luv[1] = 0.0;
+        luv[2] = 0.0;
+    }
+}
+
+ORC_API void orc_cieluv(const orc_rgbdef *d, int mode,
+                        const double *p, int n, const double *q, int m,
+                        const uint8_t *rgb, int64_t npix,
+                        double *L, double *U, double *V, int nthreads)
+{
+    orc_set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < npix; ++i) {
+        double luv[3];
+        orc_cieluv_pixel(d, mode, p, n, q, m, rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2], luv);
+        L[i] = luv[0];
+        U[i] = luv[1];
+        V[i] = luv[2];
+    }
+}
+
+/* Delta E*uv (the Euclidean distance in L*u*v*) between the MACT and the
+ * exact CIELUV, average and maximum over the 2^24 cube. */
+ORC_API void orc_cube_eps_cieluv(const orc_rgbdef *d, const double *p, int n,
+                                 const double *q, int m, double out[2])
+{
+    double sum = 0.0, mx = 0.0;
+#pragma omp parallel for reduction(+:sum) reduction(max:mx) schedule(static)
+    for (int r = 0; r < 256; ++r)
+        for (int g = 0; g < 256; ++g)
+            for (int b = 0; b < 256; ++b) {
+                double e[3], a[3];
+                orc_cieluv_pixel(d, 0, NULL, 0, NULL, 0, r, g, b, e);
+                orc_cieluv_pixel(d, 1, p, n, q, m, r, g, b, a);
+                double de = orc_delta_e(e, a);
+                sum += de;
+                if (de > mx) mx = de;
+            }
+    out[0] = sum / 16777216.0;
+    out[1] = mx;
 }
 
 /* --------------------------------------------------------------------- HSI */

@@ -96,6 +96,14 @@ MUTANTS = [
     ("eps_sct_inverse_channels", "orc_cielab_pixel(d, 0, NULL, 0, NULL, 0, back[0], back[1], back[2], a);",
      "orc_cielab_pixel(d, 0, NULL, 0, NULL, 0, back[0], back[2], back[1], a);"),
     ("cbrt_probs_channel", "c2 += t[2] > 0.008856;", "c2 += t[1] > 0.008856;"),
+    # CIELUV (CIE 1976 L*u*v*, the variant the Conclusions name)
+    ("luv_denominator_weight", "const double den = X + 15.0 * Y + 3.0 * Z;", "const double den = X + 5.0 * Y + 3.0 * Z;"),
+    ("luv_u_numerator", "luv[1] = 13.0 * L * (4.0 * X / den - un);", "luv[1] = 13.0 * L * (4.0 * Y / den - un);"),
+    ("luv_v_white_term", "luv[2] = 13.0 * L * (9.0 * Y / den - vn);", "luv[2] = 13.0 * L * (9.0 * Y / den - un);"),
+    ("luv_lightness_channel", "const double fy = mode ? orc_f_approx(t[1], p, n, q, m) : orc_f_exact(t[1]);",
+     "const double fy = mode ? orc_f_approx(t[0], p, n, q, m) : orc_f_exact(t[0]);"),
+    ("luv_white_u_numerator", "const double un = 4.0 * Xn / dn, vn = 9.0 * Yn / dn;",
+     "const double un = 4.0 * Yn / dn, vn = 9.0 * Yn / dn;"),
 ]
 
 TWO_PI = 2.0 * math.pi
@@ -272,7 +280,30 @@ def pin_printed_cube_errors():
     assert abs(a - float(row[2])) <= 1e-6 and abs(b - float(row[3])) <= 2e-6
 
 
-PINS = [pin_primaries_lab, pin_grays, pin_hsi_primaries, pin_sct_primaries, pin_sct_round_trip, pin_distances,
+def pin_cieluv():
+    """CIELUV: L* equals CIELAB's L*; grays have u* = v* = 0; the primaries'
+    u', v' recovered from u*, v* and L* equal the CIE 1976 UCS values of the
+    ITU-R BT.709 chromaticities (tests/golden/bt709_chromaticities.txt)."""
+    rgb = np.random.default_rng(4).integers(0, 256, (3000, 3)).astype(np.uint8)
+    for exact in (True, False):
+        assert np.array_equal(O.cieluv(rgb, exact=exact)[0], O.cielab(rgb, exact=exact)[0])
+    v = np.arange(256, dtype=np.uint8)
+    _, U, V = O.cieluv(np.stack([v, v, v], axis=1), exact=True)
+    assert np.abs(U).max() < 1e-9 and np.abs(V).max() < 1e-9
+    rows = {r[0]: r[1:] for r in read_golden("bt709_chromaticities.txt")}
+
+    def uv(x, y):
+        d = -2.0 * x + 12.0 * y + 3.0
+        return 4.0 * x / d, 9.0 * y / d
+    un, vn = uv(float(rows["white"][3]), float(rows["white"][4]))
+    for name in ("red", "green", "blue"):
+        r, g, b, x, y = rows[name]
+        L, U, V = O.cieluv(_px([int(r), int(g), int(b)]), exact=True)
+        ur, vr = uv(float(x), float(y))
+        assert abs(U[0] / (13.0 * L[0]) + un - ur) < 2e-5 and abs(V[0] / (13.0 * L[0]) + vn - vr) < 2e-5, name
+
+
+PINS = [pin_primaries_lab, pin_grays, pin_cieluv, pin_hsi_primaries, pin_sct_primaries, pin_sct_round_trip, pin_distances,
         pin_lut_linear_reproduction, pin_lut_nodes, pin_hsi_lut_nodes, pin_gradient_finite_differences,
         pin_probabilities, pin_printed_cube_errors]
 
