@@ -4,7 +4,8 @@ Workload (one step): every 24-bit colour (2^24 pixels, lexicographic, one
 4096 x 4096 uint8 image) converted by each per-pixel row of the hot path:
 MACT RGB->CIELAB (4,4), HSI (n=5), SCT (5,5,5); the exact (libm) forms of
 the three; and trilinear / prism / pyramidal / tetrahedral interpolation in
-17^3 and 33^3 FP32 LUTs -- 14 conversions, FP32 planar output.
+17^3 and 33^3 FP32 LUTs (built and packed to 16-byte nodes once, before the
+timed region) -- 14 conversions, FP32 planar output.
 
 value = pixel-conversions per second over the whole step (14 x 2^24 pixels
 per step per GPU), in Gpix/s; the MACT CIELAB row's own Gpix/s and HBM
@@ -27,6 +28,7 @@ arm) on a bounded sample of the same workload.
 """
 import argparse
 import collections
+import gc
 import json
 import os
 import statistics
@@ -187,7 +189,9 @@ def run_gpu(args):
     cube = synth.rgb_cube()
     cube_h = torch.from_numpy(cube)
     inputs = [cube_h.to(dev) for _ in range(IN_COPIES)]
-    luts = {n: mact.mact_lut_build(h_mact, n, device=dev) for n in (17, 33)}
+    # the LUTs are built and packed to 16-byte nodes once, outside the timed
+    # region (mact_lut_pack: the layout the kernels read)
+    luts = {n: mact.mact_lut_pack(h_mact, mact.mact_lut_build(h_mact, n, device=dev)) for n in (17, 33)}
     outs = {name: torch.empty((3, 4096, 4096), dtype=torch.float32, device=dev) for name, _, _ in ROWS}
     torch.cuda.synchronize()
 
@@ -198,7 +202,7 @@ def run_gpu(args):
             mact.mact_convert(h_exact, rgb, arg, out=out, stream=stream)
         else:
             m, n = arg
-            mact.mact_lut_interp(h_mact, m, luts[n], rgb, out=out.view(3, -1), stream=stream)
+            mact.mact_lut_interp_packed(h_mact, m, luts[n], rgb, out=out.view(3, -1), stream=stream)
 
     ev = {name: [] for name, _, _ in ROWS}
 
@@ -306,7 +310,7 @@ def run_gpu(args):
             large = large_headline(args.steps)
         if not args.no_served:
             served = serve_experiment(args.served_seconds, paths=("direct", "direct_fitted66", "plain"),
-                                      ring_bytes=4 << 30, budget=16 << 30)
+                                      ring_bytes=8 << 30, budget=16 << 30)
         clk_more = more.stop()
 
     if rank == 0:
@@ -588,7 +592,8 @@ def run_grad_workload(args):
 
 
 def run_lut_workload(args):
-    """Standard vs caching LUT layout, 4 methods x {9, 17, 33}^3, on the
+    """Standard (packed float3, 16-byte copy made per call above 17^3), packed
+    once (mact_lut_pack) and caching LUT layouts, 4 methods x {9, 17, 33}^3, on the
     2^24-colour cube (coherent) and on i.i.d. uniform noise (incoherent); and
     HSI through a 17^3 / 33^3 LUT with angular hue interpolation beside the
     exact and MACT HSI transforms."""
@@ -605,13 +610,16 @@ def run_lut_workload(args):
     rows = {}
     for n in (9, 17, 33):
         lut = mact.mact_lut_build(h, n, device=dev)
+        lut4 = mact.mact_lut_pack(h, lut)
         cache = mact.mact_lut_cache_build(h, lut)
         for name, x in inputs.items():
             xs = [x.clone() for _ in range(4)]
             for m in ("trilinear", "prism", "pyramid", "tetra"):
-                for layout in ("standard", "caching"):
+                for layout in ("standard", "packed", "caching"):
                     if layout == "standard":
                         fn = lambda v: mact.mact_lut_interp(h, m, lut, v, out=out)
+                    elif layout == "packed":
+                        fn = lambda v: mact.mact_lut_interp_packed(h, m, lut4, v, out=out)
                     else:
                         fn = lambda v: mact.mact_lut_interp_cached(h, m, cache, n, v, out=out)
                     for i in range(3):
@@ -828,7 +836,8 @@ def serve_experiment(seconds, paths=("direct", "staged", "direct_fitted66", "pla
                                                    "queue_p99_ms", "h2d_p99_ms", "compute_p99_ms", "d2h_p99_ms")}
         stages["d2h_busy_ms"] = round(st["d2h_busy_ms"], 1)
         stages["d2h_copy_gbs"] = round(st["d2h_copy_gbs"], 1)
-        return summary(lat, npx, wall, {"mode": mode, "budget_bytes": budget, "batches": st["batches"],
+        return summary(lat, npx, wall, {"mode": mode, "budget_bytes": budget,
+                                        "admitted_bytes_max": int(st["inflight_bytes_max"]), "batches": st["batches"],
                                         "server_p50_ms": round(st["p50_ms"], 3),
                                         "server_p99_ms": round(st["p99_ms"], 3), "server_stages_ms": stages,
                                         "client": stats})
@@ -859,8 +868,22 @@ def serve_experiment(seconds, paths=("direct", "staged", "direct_fitted66", "pla
             npx += hgt * wid
         return summary(lat, npx, time.perf_counter() - t0)
 
-    runners = {"direct": lambda tr: served(tr, "direct"), "staged": lambda tr: served(tr, "staged"),
-               "direct_fitted66": lambda tr: served(tr, "direct", h66), "plain": plain}
+    def quiet(fn):
+        """Run one path of the trace with Python's cyclic garbage collector
+        off (collected first): a collection pause of tens of milliseconds in
+        the load generator delays every arrival behind it, and the burst it
+        then submits shows as server latency."""
+        def run(tr):
+            gc.collect()
+            gc.disable()
+            try:
+                return fn(tr)
+            finally:
+                gc.enable()
+        return run
+
+    runners = {"direct": quiet(lambda tr: served(tr, "direct")), "staged": quiet(lambda tr: served(tr, "staged")),
+               "direct_fitted66": quiet(lambda tr: served(tr, "direct", h66)), "plain": quiet(plain)}
     for p in paths:
         runners[p](warm_trace)
 

@@ -42,7 +42,9 @@
  *      HSI:    H in radians [0, 2 pi), S and I in [0, 1] with R = R'/255;
  *              H = 0 where max == min (hue undefined), S = 0 for black;
  *      SCT:    L in 8-bit code units [0, 441.7], angle A and angle B in
- *              radians; black gives (0, 0, 0), R = G = 0 gives B = 0.
+ *              radians; black gives (0, 0, 0), R = G = 0 gives B = 0;
+ *      CIELUV: L*, u*, v* in CIE 1976 units (white = 100, 0, 0); black
+ *              gives (0, 0, 0).
  */
 #ifndef MACT_H
 #define MACT_H
@@ -69,7 +71,10 @@ typedef enum {
     MACT_E_BUSY = -6         /* no free slot; retry later */
 } mact_status;
 
-typedef enum { MACT_CIELAB = 0, MACT_HSI = 1, MACT_SCT = 2 } mact_space;
+/* MACT_CIELUV: CIE 1976 L*u*v*, the variant the paper's Conclusions name
+ * (the same cube-root approximant in L*; u* = 13 L* (u' - u'n),
+ * v* = 13 L* (v' - v'n), u' = 4X / (X + 15Y + 3Z), v' = 9Y / (X + 15Y + 3Z)). */
+typedef enum { MACT_CIELAB = 0, MACT_HSI = 1, MACT_SCT = 2, MACT_CIELUV = 3 } mact_space;
 typedef enum { MACT_F32 = 0, MACT_F16 = 1 } mact_dtype;
 typedef enum { MACT_TRILINEAR = 0, MACT_PRISM = 1, MACT_PYRAMID = 2, MACT_TETRA = 3 } mact_interp;
 
@@ -269,6 +274,24 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
                             const uint8_t *d_rgb, int64_t npix, float *const d_out[3],
                             int32_t *d_sel, mact_stream stream);
 
+/* The same LUT with every node padded to 16 bytes, for repeated
+ * interpolation: d_lut4[(((i*n + j)*n + k)*4 + c] = d_lut[((i*n + j)*n + k)*3 + c]
+ * for c < 3, and 0 for c = 3.  A LUT with n <= 17 is staged whole in every
+ * CTA's shared memory; a larger one (33^3: 575 KB) is read through L1 as
+ * 16-byte nodes.  mact_lut_interp repacks such a LUT into handle scratch on
+ * every call (and serialises calls on one handle that share that scratch);
+ * packing once with mact_lut_pack and calling mact_lut_interp_packed avoids
+ * both.  d_lut4 holds n^3 * 4 floats, is owned by the caller and must be
+ * 16-byte aligned, else MACT_E_INVAL.  The paper has no counterpart: it is a
+ * memory layout of the same LUT. */
+mact_status mact_lut_pack(mact_handle h, const float *d_lut, int32_t n, float *d_lut4, mact_stream stream);
+
+/* mact_lut_interp on a packed LUT (d_lut4 from mact_lut_pack): the same
+ * cells, simplices, selection ids and values. */
+mact_status mact_lut_interp_packed(mact_handle h, int32_t method, const float *d_lut4, int32_t n,
+                                   const uint8_t *d_rgb, int64_t npix, float *const d_out[3],
+                                   int32_t *d_sel, mact_stream stream);
+
 /* ---- differentiable RGB -> CIELAB ----------------------------------------
  * Input d_x is LINEAR RGB (the output of Eq. equ_rgb_lin, e.g. a network's
  * activations) as planar FP32 of shape (nbatch, 3, hw): plane c of image b
@@ -302,9 +325,12 @@ mact_status mact_lab_delta_e_loss(mact_handle h, const float *d_x, const float *
 /* ---- served form -------------------------------------------------------
  * A conversion server with continuous batching (the paper has no serving
  * layer; its transforms are what each request runs).  One scheduler thread
- * per server admits queued requests in arrival order while a slot is free
- * and the staging arena (mem_budget_bytes of device memory, allocated once by
- * mact_serve_create) has room for the request's staged input and output,
+ * per server admits queued requests in arrival order while a slot is free,
+ * the input and output bytes of all admitted, unfinished requests stay
+ * within mem_budget_bytes (in either mode, whether their buffers are used in
+ * place or staged), and, for staged buffers, the staging arena
+ * (mem_budget_bytes of device memory, allocated once by mact_serve_create)
+ * has room for the request's staged input and output;
  * converts every request admitted in one tick with one launch of the batched
  * kernel (as mact_convert_batch), and copies results back, on three streams
  * (H2D, compute, D2H) so the copies of one tick overlap the kernel of
@@ -341,12 +367,15 @@ typedef struct {
      * D2H stream reaches a request's copies to their end) and the bandwidth
      * they ran at (bytes / that time). */
     double d2h_busy_ms, d2h_copy_gbs;
+    /* Largest sum of admitted requests' input and output bytes seen (never
+     * above the budget). */
+    int64_t inflight_bytes_max;
 } mact_serve_stats_t;
 
 /* Create a server for handle h (on h's device), in direct mode.  max_slots
  * bounds the number of admitted, unfinished requests (1..65536);
- * mem_budget_bytes (>= 4096) bounds their staging memory.  Device-resident
- * inputs and outputs, and host buffers used in place, take no budget.
+ * mem_budget_bytes (>= 4096) bounds the input and output bytes of the
+ * admitted requests, and is the size of the staging arena.
  * A tick that fails leaves its requests failed (MACT_E_CUDA from poll and
  * wait, with the reason in mact_last_error) and returns their staging
  * memory once the server's streams have drained.  For testing that path,
@@ -363,7 +392,7 @@ mact_status mact_serve_set_mode(mact_server_t srv, int32_t mode);
  * is fastest; staged pageable memory works but its copies block the
  * scheduler) or device memory.  The buffers must stay valid until the
  * request is done.  Returns a ticket.  MACT_E_NOMEM if the
- * request alone needs more staging than the whole budget; MACT_E_BUSY once
+ * request's input and output alone exceed the whole budget; MACT_E_BUSY once
  * the server is shutting down. */
 mact_status mact_serve_submit(mact_server_t srv, const mact_image *img, uint64_t *ticket);
 

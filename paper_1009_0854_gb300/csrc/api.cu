@@ -109,6 +109,24 @@ static mact_status build_coeffs(const mact_config &cfg, Coeffs &co)
         // white (k = 1,1,1) must map to t <= 1: the cube-root fits live on [0.008856, 1]
         if (rowsum / d.white[c] > 1.0 + 1e-6) return inval("RGB definition maps white above the reference white");
     }
+    {
+        // CIE 1976 u', v' terms (the CIELUV variant)
+        const double Xn = d.white[0], Yn = d.white[1], Zn = d.white[2];
+        const double dn = Xn + 15.0 * Yn + 3.0 * Zn;
+        const double den[3] = {Xn, 15.0 * Yn, 3.0 * Zn};
+        for (int c = 0; c < 3; ++c) {
+            co.luv_den64[c] = den[c];
+            co.luv_den[c] = (float)den[c];
+        }
+        co.luv_u64 = 4.0 * Xn;
+        co.luv_v64 = 9.0 * Yn;
+        co.luv_un64 = 4.0 * Xn / dn;
+        co.luv_vn64 = 9.0 * Yn / dn;
+        co.luv_c[0] = (float)(4.0 * Xn * 15.0 * Yn / dn);
+        co.luv_c[1] = (float)(9.0 * Yn * Xn / dn);
+        co.luv_c[2] = (float)(4.0 * Xn * 3.0 * Zn / dn);
+        co.luv_c[3] = (float)(9.0 * Yn * 3.0 * Zn / dn);
+    }
     if (!(d.gamma_slope > 0.0) || !(d.gamma_exponent > 0.0) || !(d.gamma_offset > -1.0) ||
         !std::isfinite(d.gamma_threshold))
         return inval("invalid gamma parameters");
@@ -212,7 +230,7 @@ mact_status check_image(const mact_image *img)
 {
     if (!img) return inval("image is NULL");
     if (img->width < 0 || img->height < 0) return inval("negative image size");
-    if (img->space < MACT_CIELAB || img->space > MACT_SCT) return inval("unknown space");
+    if (img->space < MACT_CIELAB || img->space > MACT_CIELUV) return inval("unknown space");
     if (img->dtype != MACT_F32 && img->dtype != MACT_F16) return inval("unknown dtype");
     if (img->width == 0 || img->height == 0) return MACT_OK;
     // at most 2^42 pixels: tile indices stay below 2^31
@@ -488,7 +506,7 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
     if (st != MACT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (!lut_needs_pack(n))
-        return cuda_status(launch_lut_interp(*h, method, d_lut, n, d_rgb, npix, d_out, d_sel, nullptr, s),
+        return cuda_status(launch_lut_interp(*h, method, d_lut, nullptr, n, d_rgb, npix, d_out, d_sel, s),
                            "mact_lut_interp launch");
     // large LUT: repack into the handle's float4 buffer, read by the kernel
     std::lock_guard<std::mutex> lock(h->lut_mu);
@@ -505,9 +523,46 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
     }
     e = cudaStreamWaitEvent(s, h->ev_lut, 0);   // previous reader of the buffer (any stream)
     if (e == cudaSuccess) e = launch_lut_pack4(d_lut, n, h->d_lut4, s);
-    if (e == cudaSuccess) e = launch_lut_interp(*h, method, d_lut, n, d_rgb, npix, d_out, d_sel, h->d_lut4, s);
+    if (e == cudaSuccess) e = launch_lut_interp(*h, method, nullptr, h->d_lut4, n, d_rgb, npix, d_out, d_sel, s);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_lut, s);
     return cuda_status(e, "mact_lut_interp launch");
+}
+
+mact_status mact_lut_pack(mact_handle h, const float *d_lut, int32_t n, float *d_lut4, mact_stream stream)
+{
+    if (!h) return inval("mact_lut_pack: NULL handle");
+    if (n < 2 || n > 64) return inval("LUT size must be 2..64");
+    if (!d_lut || !d_lut4) return inval("NULL pointer");
+    if (!aligned4(d_lut)) return inval("d_lut not 4-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(d_lut4) & 15) != 0) return inval("d_lut4 must be 16-byte aligned");
+    mact_status st = check_access(*h, d_lut, "d_lut");
+    if (st == MACT_OK) st = check_access(*h, d_lut4, "d_lut4");
+    if (st != MACT_OK) return st;
+    return cuda_status(launch_lut_pack4(d_lut, n, reinterpret_cast<float4 *>(d_lut4), (cudaStream_t)stream),
+                       "mact_lut_pack launch");
+}
+
+mact_status mact_lut_interp_packed(mact_handle h, int32_t method, const float *d_lut4, int32_t n,
+                                   const uint8_t *d_rgb, int64_t npix, float *const d_out[3], int32_t *d_sel,
+                                   mact_stream stream)
+{
+    if (!h) return inval("mact_lut_interp_packed: NULL handle");
+    if (method < MACT_TRILINEAR || method > MACT_TETRA) return inval("unknown interpolation method");
+    if (n < 2 || n > 64) return inval("LUT size must be 2..64");
+    if (npix < 0 || npix > (int64_t(1) << 42)) return inval("pixel count out of range");
+    if (npix == 0) return MACT_OK;
+    if (!d_lut4 || !d_rgb || !d_out || !d_out[0] || !d_out[1] || !d_out[2]) return inval("NULL pointer");
+    if ((reinterpret_cast<uintptr_t>(d_lut4) & 15) != 0) return inval("d_lut4 must be 16-byte aligned");
+    if (!aligned4(d_out[0]) || !aligned4(d_out[1]) || !aligned4(d_out[2]) || !aligned4(d_sel))
+        return inval("d_out[] and d_sel must be 4-byte aligned");
+    mact_status st = check_access(*h, d_lut4, "d_lut4");
+    if (st == MACT_OK) st = check_access(*h, d_rgb, "d_rgb");
+    for (int c = 0; c < 3 && st == MACT_OK; ++c) st = check_access(*h, d_out[c], "d_out");
+    if (st == MACT_OK) st = check_access(*h, d_sel, "d_sel");
+    if (st != MACT_OK) return st;
+    return cuda_status(launch_lut_interp(*h, method, nullptr, reinterpret_cast<const float4 *>(d_lut4), n, d_rgb,
+                                         npix, d_out, d_sel, (cudaStream_t)stream),
+                       "mact_lut_interp_packed launch");
 }
 
 // ---- differentiable RGB -> CIELAB ------------------------------------------

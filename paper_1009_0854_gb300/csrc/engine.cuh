@@ -157,12 +157,12 @@ __device__ __forceinline__ void stage_bytes(uint4 *sbuf, const uint8_t *in, int 
     for (int i = i0 + threadIdx.x; i < nb; i += THREADS) sb[i] = in[i];
 }
 
+// The compute half of the guarded path: sbuf already holds the tile's
+// 3*cnt input bytes (staged and synchronised by the caller).
 template <int THREADS, int SUBS, typename OutT, bool SEL, class Op>
-__device__ __forceinline__ void compute_guarded(uint4 *sbuf, const uint8_t *in, int cnt, const Op &op, OutT *o0,
-                                                OutT *o1, OutT *o2, int32_t *sel)
+__device__ __forceinline__ void compute_guarded_staged(const uint4 *sbuf, int cnt, const Op &op, OutT *o0,
+                                                       OutT *o1, OutT *o2, int32_t *sel)
 {
-    stage_bytes<THREADS>(sbuf, in, 3 * cnt);
-    __syncthreads();
     for (int s = 0; s < SUBS; ++s) {
         const int p = s * TileShape<THREADS>::sub + kPxPerThread * threadIdx.x;
         if (p >= cnt) break;
@@ -179,6 +179,15 @@ __device__ __forceinline__ void compute_guarded(uint4 *sbuf, const uint8_t *in, 
             }
         }
     }
+}
+
+template <int THREADS, int SUBS, typename OutT, bool SEL, class Op>
+__device__ __forceinline__ void compute_guarded(uint4 *sbuf, const uint8_t *in, int cnt, const Op &op, OutT *o0,
+                                                OutT *o1, OutT *o2, int32_t *sel)
+{
+    stage_bytes<THREADS>(sbuf, in, 3 * cnt);
+    __syncthreads();
+    compute_guarded_staged<THREADS, SUBS, OutT, SEL>(sbuf, cnt, op, o0, o1, o2, sel);
 }
 
 // Partial tile (cnt < px pixels) with element-aligned outputs: staged like

@@ -48,7 +48,8 @@ struct mact_ctx {
     int batch_next = 0;
     mact::BatchCfg batch_cfg;            // used by mact_convert_batch and new plans
 
-    // LUT interpolation: float4 copy of a large LUT (n > 17), grown on demand
+    // LUT interpolation from an unpacked LUT with n > 17: float4 copy,
+    // repacked on every call, grown on demand
     std::mutex lut_mu;
     float4 *d_lut4 = nullptr;
     int64_t lut4_cap = 0;                // nodes
@@ -77,11 +78,25 @@ cudaError_t launch_batch_param(const mact_ctx &h, const ParamList &list, int32_t
 int batch_blocks_per_sm(const mact_ctx &h, const BatchCfg &cfg = BatchCfg());
 bool batch_cfg_supported(const BatchCfg &cfg);
 
+constexpr int kLutSmemMaxN = 17;   // largest LUT staged whole in every CTA's shared memory
+
+// k_lut_inst.cu (one object per method): interpolation from a packed float3
+// LUT (lut) or a float4 copy (lut4), and from the caching layout
+template <int METHOD, bool SEL>
+cudaError_t lut_interp_method(const mact_ctx &h, const float *lut, const float4 *lut4, int n, const uint8_t *rgb,
+                              int64_t npix, float *const out[3], int32_t *sel, cudaStream_t s);
+template <int METHOD, bool SEL>
+cudaError_t lut_cached_method(const mact_ctx &h, const float4 *cache, int n, const uint8_t *rgb, int64_t npix,
+                              float *const out[3], int32_t *sel, cudaStream_t s);
+
 // k_lut.cu
 cudaError_t launch_lut_build(const mact_ctx &h, int n, float *d_lut, cudaStream_t s);
-cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut, int n,
-                              const uint8_t *d_rgb, int64_t npix, float *const out[3],
-                              int32_t *d_sel, const float4 *d_lut4, cudaStream_t s);
+// nodes from d_lut4 (float4) when given, else from d_lut (packed float3);
+// n > 17 needs d_lut4
+cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut, const float4 *d_lut4, int n,
+                              const uint8_t *d_rgb, int64_t npix, float *const out[3], int32_t *d_sel,
+                              cudaStream_t s);
+bool lut_needs_pack(int n);
 cudaError_t launch_lut_pack4(const float *d_lut, int n, float4 *d_lut4, cudaStream_t s);
 cudaError_t launch_lut_cache_build(const float *d_lut, int n, float4 *d_cache, cudaStream_t s);
 
@@ -93,7 +108,6 @@ cudaError_t launch_lut_interp_hsi(const mact_ctx &h, const float4 *d_lut4, int n
 cudaError_t launch_lut_interp_cached(const mact_ctx &h, int method, const float4 *d_cache, int n,
                                      const uint8_t *d_rgb, int64_t npix, float *const out[3], int32_t *d_sel,
                                      cudaStream_t s);
-bool lut_needs_pack(int n);
 
 // k_grad.cu
 cudaError_t launch_lab_forward(const mact_ctx &h, const float *x, int64_t nb, int64_t hw, float *lab,

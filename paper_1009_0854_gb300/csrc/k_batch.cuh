@@ -1,7 +1,8 @@
 // k_batch.cuh -- the batched conversion kernels (a tile work list over many
 // images of any spaces and dtypes) and their launchers.  Included only by
-// the per-form translation units k_batch_*.cu, each of which instantiates
-// one cube-root form with MACT_BATCH_FORM.
+// k_batch_inst.cu, which the build compiles once per (cube-root form, launch
+// shape) pair, each object instantiating one pair with MACT_BATCH_SHAPE, so
+// the 20 pairs compile in parallel.
 //
 // The device-list kernel pulls tiles with an atomic counter, so uneven
 // images and spaces balance dynamically across CTAs; its last CTA resets the
@@ -18,7 +19,10 @@ __device__ __forceinline__ void batch_tile(const ImageDesc &im, int64_t t, const
 {
     float *scr = reinterpret_cast<float *>(sbuf + TileShape<THREADS, SUBS>::vecs);
     if (im.space == MACT_CIELAB) {
-        const OpCielab<EXACT, RDEG> op{sgam, co};
+        const OpCielab<EXACT, RDEG, sizeof(OutT) == 4> op{sgam, co};   // FP16 planes: no Newton step
+        process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr, scr);
+    } else if (im.space == MACT_CIELUV) {
+        const OpCieluv<EXACT, RDEG, sizeof(OutT) == 4> op{sgam, co};
         process_tile<THREADS, OutT, false, decltype(op), SUBS>(im, t, op, sbuf, nullptr, scr);
     } else if (im.space == MACT_HSI) {
         const OpHsi<EXACT> op{co};
@@ -103,85 +107,45 @@ k_batch_param(const __grid_constant__ ParamList list, int32_t count, int64_t tot
     }
 }
 
-template <bool EXACT, int RDEG, int THREADS, int SUBS>
-static int occ_batch()
+// Per-shape entry points (declared in convert_common.cuh): resident CTAs per
+// SM, and launches from a device work list or a by-value list.
+template <bool EXACT, int RDEG, int T, int S>
+int batch_occ_shape()
 {
     static const int occ = [] {   // thread-safe one-time init
         int o = 0, op = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch<EXACT, RDEG, THREADS, SUBS>,
-                                                                      THREADS, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch<EXACT, RDEG, T, S>, T, 0);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_batch_param<EXACT, RDEG, THREADS, SUBS>,
-                                                              THREADS, 0);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_batch_param<EXACT, RDEG, T, S>, T, 0);
         if (op < o) o = op;   // one figure serves both forms
         return (e != cudaSuccess || o <= 0) ? 1 : o;
     }();
     return occ;
 }
 
-template <bool EXACT, int RDEG>
-static int occ_shape(const BatchCfg &cfg)
+template <bool EXACT, int RDEG, int T, int S>
+cudaError_t batch_launch_shape(const mact_ctx &h, const ImageDesc *d_imgs, int32_t count, int64_t total,
+                               unsigned long long *d_ctr, int grid, cudaStream_t s)
 {
-#define MACT_OCC(T, S) if (cfg.threads == T && cfg.subs == S) return occ_batch<EXACT, RDEG, T, S>();
-    MACT_BATCH_SHAPES(MACT_OCC)
-#undef MACT_OCC
-    return 1;
+    k_batch<EXACT, RDEG, T, S><<<grid, T, 0, s>>>(d_imgs, count, total, d_ctr, h.co, h.d_gamma);
+    return cudaGetLastError();
 }
 
-template <bool EXACT, int RDEG>
-static cudaError_t launch_shape(const mact_ctx &h, const ImageDesc *d_imgs, int32_t count, int64_t total,
-                                unsigned long long *d_ctr, int grid, cudaStream_t s, const BatchCfg &cfg)
+template <bool EXACT, int RDEG, int T, int S>
+cudaError_t batch_launch_param_shape(const mact_ctx &h, const ParamList &list, int32_t count, int64_t total,
+                                     int grid, cudaStream_t s)
 {
-#define MACT_LAUNCH(T, S)                                                                               \
-    if (cfg.threads == T && cfg.subs == S) {                                                            \
-        k_batch<EXACT, RDEG, T, S><<<grid, T, 0, s>>>(d_imgs, count, total, d_ctr, h.co, h.d_gamma);     \
-        return cudaGetLastError();                                                                      \
-    }
-    MACT_BATCH_SHAPES(MACT_LAUNCH)
-#undef MACT_LAUNCH
-    return cudaErrorInvalidValue;
-}
-
-template <bool EXACT, int RDEG>
-static cudaError_t launch_shape_param(const mact_ctx &h, const ParamList &list, int32_t count, int64_t total,
-                                      int grid, cudaStream_t s, const BatchCfg &cfg)
-{
-#define MACT_LAUNCH(T, S)                                                                               \
-    if (cfg.threads == T && cfg.subs == S) {                                                            \
-        k_batch_param<EXACT, RDEG, T, S><<<grid, T, 0, s>>>(list, count, total, h.co, h.d_gamma);        \
-        return cudaGetLastError();                                                                      \
-    }
-    MACT_BATCH_SHAPES(MACT_LAUNCH)
-#undef MACT_LAUNCH
-    return cudaErrorInvalidValue;
-}
-
-template <bool EXACT, int RDEG>
-int batch_occ(const BatchCfg &cfg)
-{
-    return occ_shape<EXACT, RDEG>(cfg);
-}
-
-template <bool EXACT, int RDEG>
-cudaError_t batch_launch(const mact_ctx &h, const ImageDesc *d_imgs, int32_t count, int64_t total,
-                         unsigned long long *d_ctr, int grid, cudaStream_t s, const BatchCfg &cfg)
-{
-    return launch_shape<EXACT, RDEG>(h, d_imgs, count, total, d_ctr, grid, s, cfg);
-}
-
-template <bool EXACT, int RDEG>
-cudaError_t batch_launch_param(const mact_ctx &h, const ParamList &list, int32_t count, int64_t total, int grid,
-                               cudaStream_t s, const BatchCfg &cfg)
-{
-    return launch_shape_param<EXACT, RDEG>(h, list, count, total, grid, s, cfg);
+    k_batch_param<EXACT, RDEG, T, S><<<grid, T, 0, s>>>(list, count, total, h.co, h.d_gamma);
+    return cudaGetLastError();
 }
 
 }  // namespace mact
 
-// Explicit instantiation of one form's entry points (inside namespace mact).
-#define MACT_BATCH_FORM(EXACT, RDEG)                                                                        \
-    template int batch_occ<EXACT, RDEG>(const BatchCfg &);                                                   \
-    template cudaError_t batch_launch<EXACT, RDEG>(const mact_ctx &, const ImageDesc *, int32_t, int64_t,    \
-                                                   unsigned long long *, int, cudaStream_t, const BatchCfg &); \
-    template cudaError_t batch_launch_param<EXACT, RDEG>(const mact_ctx &, const ParamList &, int32_t, int64_t, \
-                                                         int, cudaStream_t, const BatchCfg &);
+// Explicit instantiation of one (form, shape) pair's entry points (inside
+// namespace mact).
+#define MACT_BATCH_SHAPE(EXACT, RDEG, T, S)                                                                  \
+    template int batch_occ_shape<EXACT, RDEG, T, S>();                                                        \
+    template cudaError_t batch_launch_shape<EXACT, RDEG, T, S>(const mact_ctx &, const ImageDesc *, int32_t,  \
+                                                               int64_t, unsigned long long *, int, cudaStream_t); \
+    template cudaError_t batch_launch_param_shape<EXACT, RDEG, T, S>(const mact_ctx &, const ParamList &,     \
+                                                                     int32_t, int64_t, int, cudaStream_t);

@@ -56,12 +56,18 @@ static cudaError_t dispatch_space(const mact_ctx &h, const ImageDesc &im, cudaSt
 {
     const bool exact = h.cfg.exact != 0;
     const bool rat = h.co.lab_rational != 0;
+    constexpr bool NR = sizeof(OutT) == 4;   // Newton step on the reciprocal for FP32 planes only
     switch (im.space) {
     case MACT_CIELAB:
         if (exact) return launch_one<OpCielab<true, 4>, OutT, kTable32>(h, im, s);
-        if (rat && h.co.lab_deg == 6) return launch_one<OpCielab<false, 6>, OutT, kTable32>(h, im, s);
-        if (rat) return launch_one<OpCielab<false, 4>, OutT, kTable32>(h, im, s);
+        if (rat && h.co.lab_deg == 6) return launch_one<OpCielab<false, 6, NR>, OutT, kTable32>(h, im, s);
+        if (rat) return launch_one<OpCielab<false, 4, NR>, OutT, kTable32>(h, im, s);
         return launch_one<OpCielab<false, 0>, OutT, kTable64>(h, im, s);
+    case MACT_CIELUV:
+        if (exact) return launch_one<OpCieluv<true, 4>, OutT, kTable32>(h, im, s);
+        if (rat && h.co.lab_deg == 6) return launch_one<OpCieluv<false, 6, NR>, OutT, kTable32>(h, im, s);
+        if (rat) return launch_one<OpCieluv<false, 4, NR>, OutT, kTable32>(h, im, s);
+        return launch_one<OpCieluv<false, 0>, OutT, kTable64>(h, im, s);
     case MACT_HSI:
         if (exact) return launch_one<WithTable<OpHsi<true>>, OutT, kNoTable>(h, im, s);
         return launch_one<WithTable<OpHsi<false>>, OutT, kNoTable>(h, im, s);

@@ -28,13 +28,19 @@ constexpr float kLinOffset = 16.0f / 116.0f;
 // with it, so the worst a* error over the 2^24 colours drops from ~2.2e-4
 // (p/q) to ~1.2e-4.
 // DEG: Horner degree of both chains (4 for the printed rationals, 6 for the
-// library's fits up to (6, 6); higher coefficients are zero).
-template <int DEG>
+// library's fits up to (6, 6); higher coefficients are zero).  The two
+// chains run together on one packed FP32 pair (lane x: d, lane y: q), one
+// f32x2 FMA per degree; each lane rounds exactly like the scalar fmaf chain.
+// NR: refine the reciprocal with a Newton step (FP32 planes); FP16 planes
+// round far more coarsely than the step's correction, so they skip it.
+template <int DEG, bool NR = true>
 __device__ __forceinline__ float f_mact(float t, const Coeffs &co)
 {
-    float d = horner<DEG>(co.lab_d, t);
-    float q = horner<DEG>(co.lab_q, t);
-    float fa = fmaf(d, rcp_nr(q), 1.0f);
+    float2 s = make_float2(co.lab_d[DEG], co.lab_q[DEG]);
+    const float2 tt = make_float2(t, t);
+#pragma unroll
+    for (int i = DEG - 1; i >= 0; --i) s = fma2(s, tt, make_float2(co.lab_d[i], co.lab_q[i]));
+    float fa = fmaf(s.x, NR ? rcp_nr(s.y) : rcp_approx(s.y), 1.0f);
     float fl = fmaf(kLinSlope, t, kLinOffset);
     return t > kKnee ? fa : fl;
 }
@@ -59,8 +65,11 @@ __device__ __forceinline__ float f_exact(float t)
 }
 
 // RDEG: 0 = the FP64 cube-root polynomial; 4 or 6 = the rational with
-// chains of that degree (ignored when EXACT).
-template <bool EXACT, int RDEG>
+// chains of that degree (ignored when EXACT).  NR: Newton step on the
+// rational's reciprocal (off for FP16 planes).  The X and Y rows of the
+// matrix, and a* and b*, run as packed FP32 pairs (bit-identical to the
+// scalar forms).
+template <bool EXACT, int RDEG, bool NR = true>
 struct OpCielab {
     const float *gam;   // 256-entry linearisation table in shared memory
     const Coeffs &co;
@@ -80,19 +89,86 @@ struct OpCielab {
             return 0;
         }
         float k0 = gam[r], k1 = gam[g], k2 = gam[b];
-        float tx = fmaf(co.m[2], k2, fmaf(co.m[1], k1, co.m[0] * k0));
-        float ty = fmaf(co.m[5], k2, fmaf(co.m[4], k1, co.m[3] * k0));
+        // (tx, ty) = rows 0 and 1 of the matrix, tz = row 2
+        const float2 txy = fma2(make_float2(co.m[2], co.m[5]), make_float2(k2, k2),
+                                fma2(make_float2(co.m[1], co.m[4]), make_float2(k1, k1),
+                                     mul2(make_float2(co.m[0], co.m[3]), make_float2(k0, k0))));
         float tz = fmaf(co.m[8], k2, fmaf(co.m[7], k1, co.m[6] * k0));
         float fx, fy, fz;
         if (EXACT) {
-            fx = f_exact(tx); fy = f_exact(ty); fz = f_exact(tz);
+            fx = f_exact(txy.x); fy = f_exact(txy.y); fz = f_exact(tz);
         } else {
             constexpr int D = RDEG == 0 ? 4 : RDEG;   // (RDEG 0 returned above)
-            fx = f_mact<D>(tx, co); fy = f_mact<D>(ty, co); fz = f_mact<D>(tz, co);
+            fx = f_mact<D, NR>(txy.x, co); fy = f_mact<D, NR>(txy.y, co); fz = f_mact<D, NR>(tz, co);
         }
         o0 = fmaf(116.0f, fy, -16.0f);
-        o1 = 500.0f * (fx - fy);
-        o2 = 200.0f * (fy - fz);
+        const float2 ab = mul2(make_float2(500.0f, 200.0f), sub2(make_float2(fx, fy), make_float2(fy, fz)));
+        o1 = ab.x;
+        o2 = ab.y;
+        return 0;
+    }
+};
+
+// ------------------------------------------------------------------ CIELUV
+// CIE 1976 L*u*v*, the variant the Conclusions name: L* exactly as in CIELAB
+// (the same cube-root approximant, or cbrtf when EXACT), and on the
+// white-normalised t the chromaticity terms u' - u'n = 4 Xn tx / D - u'n and
+// v' - v'n = 9 Yn ty / D - v'n with D = Xn tx + 15 Yn ty + 3 Zn tz;
+// u* = 13 L* (u' - u'n), v* = 13 L* (v' - v'n).  Black (D = 0) gives
+// u* = v* = 0.  FP32 form: with dn = Xn + 15 Yn + 3 Zn, identically
+//   u' - u'n = 4 Xn (15 Yn (tx - ty) + 3 Zn (tx - tz)) / (dn D),
+//   v' - v'n = 9 Yn (Xn (ty - tx) + 3 Zn (ty - tz)) / (dn D),
+// which has no cancellation near the neutral axis (the differences of t are
+// small there and exact), like the 1 + d/q form of the cube root.  The
+// quotient uses the refined reciprocal; the u and v terms run as packed FP32
+// pairs.  RDEG 0 (the FP64 cube-root polynomial) runs in FP64, direct form.
+template <bool EXACT, int RDEG, bool NR = true>
+struct OpCieluv {
+    const float *gam;   // 256-entry linearisation table in shared memory
+    const Coeffs &co;
+    __device__ __forceinline__ int operator()(uint32_t r, uint32_t g, uint32_t b, float &o0, float &o1,
+                                              float &o2) const
+    {
+        if (!EXACT && RDEG == 0) {
+            const double *g64 = reinterpret_cast<const double *>(gam);
+            const double k0 = g64[r], k1 = g64[g], k2 = g64[b];
+            const double *m = co.m64;
+            const double tx = fma(m[2], k2, fma(m[1], k1, m[0] * k0));
+            const double ty = fma(m[5], k2, fma(m[4], k1, m[3] * k0));
+            const double tz = fma(m[8], k2, fma(m[7], k1, m[6] * k0));
+            const double L = 116.0 * f_mact_poly64(ty, co) - 16.0;
+            const double D = co.luv_den64[0] * tx + co.luv_den64[1] * ty + co.luv_den64[2] * tz;
+            o0 = D > 0.0 ? (float)L : 0.0f;
+            o1 = D > 0.0 ? (float)(13.0 * L * (co.luv_u64 * tx / D - co.luv_un64)) : 0.0f;
+            o2 = D > 0.0 ? (float)(13.0 * L * (co.luv_v64 * ty / D - co.luv_vn64)) : 0.0f;
+            return 0;
+        }
+        float k0 = gam[r], k1 = gam[g], k2 = gam[b];
+        const float2 txy = fma2(make_float2(co.m[2], co.m[5]), make_float2(k2, k2),
+                                fma2(make_float2(co.m[1], co.m[4]), make_float2(k1, k1),
+                                     mul2(make_float2(co.m[0], co.m[3]), make_float2(k0, k0))));
+        float tz = fmaf(co.m[8], k2, fmaf(co.m[7], k1, co.m[6] * k0));
+        float fy;
+        if (EXACT) {
+            fy = f_exact(txy.y);
+        } else {
+            constexpr int D = RDEG == 0 ? 4 : RDEG;
+            fy = f_mact<D, NR>(txy.y, co);
+        }
+        const float L = fmaf(116.0f, fy, -16.0f);
+        const float den = fmaf(co.luv_den[2], tz, fmaf(co.luv_den[1], txy.y, co.luv_den[0] * txy.x));
+        const float rd = den > 0.0f ? rcp_nr(den) : 0.0f;
+        // (u' - u'n, v' - v'n) in the difference form, then times 13 L*
+        const float2 d1 = sub2(txy, make_float2(txy.y, txy.x));     // (tx - ty, ty - tx)
+        const float2 d2 = sub2(txy, make_float2(tz, tz));           // (tx - tz, ty - tz)
+        const float2 num = fma2(make_float2(co.luv_c[0], co.luv_c[1]), d1,
+                                mul2(make_float2(co.luv_c[2], co.luv_c[3]), d2));
+        const float2 uv = mul2(num, make_float2(rd, rd));
+        const float l13 = 13.0f * L;
+        const float2 o = mul2(make_float2(l13, l13), uv);
+        o0 = den > 0.0f ? L : 0.0f;      // black: exactly (0, 0, 0)
+        o1 = den > 0.0f ? o.x : 0.0f;
+        o2 = den > 0.0f ? o.y : 0.0f;
         return 0;
     }
 };

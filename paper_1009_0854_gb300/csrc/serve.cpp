@@ -7,9 +7,11 @@
 // read and written in place by the kernel in direct mode (the default); the
 // others, and all host buffers in staged mode, go through a device staging
 // arena.  One scheduler thread repeats a tick:
-//   1. admit queued requests in arrival order while a slot is free and the
-//      device staging arena (the memory budget, allocated once at create)
-//      has room for the request's staged input and output;
+//   1. admit queued requests in arrival order while a slot is free, the
+//      bytes every admitted request reads and writes (its input and output,
+//      in place or staged) stay within the memory budget, and -- for staged
+//      buffers -- the device staging arena (the budget's size, allocated
+//      once at create) has room for the request's staged input and output;
 //   2. for the requests admitted in this tick: copy host inputs to their
 //      staging on the H2D stream, then -- on the compute stream, after
 //      those copies -- convert all of them with ONE launch of the batched
@@ -82,6 +84,7 @@ struct Request {
     bool in_host = false, out_host = false;   // staged through the arena (else read/written in place)
     size_t in_bytes = 0, out_bytes = 0, elem = 4;
     size_t off = 0, len = 0;   // arena range
+    size_t footprint = 0;      // input + output bytes, charged to the budget while admitted
     uint8_t *d_in = nullptr;
     void *d_out[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t ev_out = nullptr;      // before the request's output copies (D2H stream)
@@ -186,6 +189,8 @@ struct mact_server {
     // stages (admission wait on the host; on the device, the batch's input
     // copies, then kernel including its wait for the compute stream, then the
     // request's output copy including its wait for earlier output copies)
+    size_t inflight_bytes = 0;           // footprints of the admitted, unretired requests (<= budget)
+    size_t inflight_bytes_max = 0;
     std::vector<double> latencies;
     std::vector<double> st_queue, st_h2d, st_comp, st_d2h;
     double d2h_bytes = 0.0, d2h_busy_ms = 0.0;   // output copies to host: bytes, summed copy time
@@ -235,6 +240,7 @@ static bool serve_tick(mact_server *s)
         std::unique_lock<std::mutex> lk(s->mu);
         while (!s->queue.empty() && (int)s->inflight.size() + (int)batch.size() < s->max_slots) {
             Request *r = s->queue.front();
+            if (s->inflight_bytes + r->footprint > s->budget) break;   // FIFO: wait for budget
             size_t off = 0;
             if (!s->arena.alloc(r->in_bytes + r->out_bytes, &off)) break;   // FIFO: wait for room
             s->queue.pop_front();
@@ -242,6 +248,8 @@ static bool serve_tick(mact_server *s)
             r->len = r->in_bytes + r->out_bytes;
             r->state = kInFlight;
             r->t_admit = Clock::now();
+            s->inflight_bytes += r->footprint;
+            s->inflight_bytes_max = std::max(s->inflight_bytes_max, s->inflight_bytes);
             batch.push_back(r);
         }
     }
@@ -342,7 +350,10 @@ static bool serve_tick(mact_server *s)
                 if (r->ev_done) cudaEventDestroy(r->ev_done);
                 r->ev_out = r->ev_done = nullptr;
                 r->bev.reset();
-                if (releasable) s->arena.release(r->off, r->len);
+                if (releasable) {
+                    s->arena.release(r->off, r->len);
+                    s->inflight_bytes -= r->footprint;
+                }
             } else {
                 s->inflight.push_back(r);
             }
@@ -390,6 +401,7 @@ static bool serve_tick(mact_server *s)
         r->ev_out = nullptr;
         r->bev.reset();
         s->arena.release(r->off, r->len);
+        s->inflight_bytes -= r->footprint;
         s->inflight.pop_front();
         retired = true;
     }
@@ -495,10 +507,11 @@ mact_status mact_serve_submit(mact_server_t s, const mact_image *img, uint64_t *
     }
     r->in_bytes = r->in_host ? (size_t)(3 * r->pixels) : 0;
     r->out_bytes = r->out_host ? (size_t)(3 * r->pixels) * r->elem : 0;
+    r->footprint = (size_t)(3 * r->pixels) * (1 + r->elem);
     const size_t need = ((r->in_bytes + 255) & ~size_t(255)) + ((r->out_bytes + 255) & ~size_t(255));
-    if (need > s->budget) {
+    if (need > s->budget || r->footprint > s->budget) {
         delete r;
-        set_error("mact_serve_submit: request needs more staging memory than the server's budget");
+        set_error("mact_serve_submit: the request's input and output exceed the server's memory budget");
         return MACT_E_NOMEM;
     }
     r->in_bytes = (r->in_bytes + 255) & ~size_t(255);
@@ -612,6 +625,7 @@ mact_status mact_serve_stats(mact_server_t s, mact_serve_stats_t *out)
     out->queued = (int64_t)s->queue.size();
     out->in_flight = (int64_t)s->inflight.size();
     out->pixels = s->pixels_done;
+    out->inflight_bytes_max = (int64_t)s->inflight_bytes_max;
     if (!l.empty()) {
         std::sort(l.begin(), l.end());
         out->p50_ms = pct(l, 0.50);

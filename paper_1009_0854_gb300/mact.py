@@ -15,7 +15,7 @@ import torch
 
 from . import _build
 
-SPACES = {"cielab": 0, "hsi": 1, "sct": 2}
+SPACES = {"cielab": 0, "hsi": 1, "sct": 2, "cieluv": 3}
 DTYPES = {torch.float32: 0, torch.float16: 1}
 METHODS = {"trilinear": 0, "prism": 1, "pyramid": 2, "tetra": 3}
 
@@ -68,7 +68,8 @@ class ServeStats(ctypes.Structure):
                 ("compute_p50_ms", ctypes.c_double), ("d2h_p50_ms", ctypes.c_double),
                 ("queue_p99_ms", ctypes.c_double), ("h2d_p99_ms", ctypes.c_double),
                 ("compute_p99_ms", ctypes.c_double), ("d2h_p99_ms", ctypes.c_double),
-                ("d2h_busy_ms", ctypes.c_double), ("d2h_copy_gbs", ctypes.c_double)]
+                ("d2h_busy_ms", ctypes.c_double), ("d2h_copy_gbs", ctypes.c_double),
+                ("inflight_bytes_max", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -100,6 +101,8 @@ def lib():
         L.mact_lut_build.argtypes = [_VP, ctypes.c_int32, _VP, _VP]
         L.mact_lut_interp.argtypes = [_VP, ctypes.c_int32, _VP, ctypes.c_int32, _VP, ctypes.c_int64,
                                       ctypes.POINTER(_VP * 3), _VP, _VP]
+        L.mact_lut_pack.argtypes = [_VP, _VP, ctypes.c_int32, _VP, _VP]
+        L.mact_lut_interp_packed.argtypes = L.mact_lut_interp.argtypes
         L.mact_serve_create.argtypes = [_VP, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(_VP)]
         L.mact_serve_submit.argtypes = [_VP, ctypes.POINTER(Image), ctypes.POINTER(ctypes.c_uint64)]
         L.mact_serve_poll.argtypes = [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
@@ -340,6 +343,45 @@ def mact_lut_interp(h, method, lut, rgb, out=None, sel=False, stream=None):
     _check(lib().mact_lut_interp(h.ptr, m, _VP(lut.data_ptr()), n, _VP(rgb.data_ptr()), npix,
                                  ctypes.byref(ptrs), _VP(s.data_ptr() if s is not None else 0),
                                  _stream(stream)), "mact_lut_interp")
+    return (out, s) if sel else out
+
+
+def mact_lut_pack(h, lut, out=None, stream=None):
+    """The (n, n, n, 3) FP32 LUT padded to (n, n, n, 4) float4 nodes, for
+    repeated interpolation with mact_lut_interp_packed."""
+    if lut.dtype != torch.float32 or not lut.is_contiguous() or lut.dim() != 4 or lut.shape[3] != 3:
+        raise ValueError("lut must be a contiguous (n, n, n, 3) float32 tensor")
+    n = lut.shape[0]
+    if lut.shape[1] != n or lut.shape[2] != n:
+        raise ValueError("lut must be a cube (n, n, n, 3)")
+    if out is None:
+        out = torch.empty((n, n, n, 4), dtype=torch.float32, device=lut.device)
+    _need(out, "out", (n, n, n, 4))
+    _check(lib().mact_lut_pack(h.ptr, _VP(lut.data_ptr()), n, _VP(out.data_ptr()), _stream(stream)), "mact_lut_pack")
+    return out
+
+
+def mact_lut_interp_packed(h, method, lut4, rgb, out=None, sel=False, stream=None):
+    """mact_lut_interp on a LUT packed by mact_lut_pack ((n, n, n, 4))."""
+    if lut4.dtype != torch.float32 or not lut4.is_contiguous() or lut4.dim() != 4 or lut4.shape[3] != 4:
+        raise ValueError("lut4 must be a contiguous (n, n, n, 4) float32 tensor")
+    if rgb.dtype != torch.uint8 or not rgb.is_contiguous() or rgb.shape[-1] != 3:
+        raise ValueError("rgb must be a contiguous (..., 3) uint8 tensor")
+    n = lut4.shape[0]
+    if lut4.shape[1] != n or lut4.shape[2] != n:
+        raise ValueError("lut4 must be a cube (n, n, n, 4)")
+    npix = rgb.numel() // 3
+    if out is None:
+        out = torch.empty((3, npix), dtype=torch.float32, device=rgb.device,
+                          pin_memory=rgb.device.type == "cpu")
+    _need(out, "out", (3, npix))
+    ptrs = (_VP * 3)(*(out[c].data_ptr() for c in range(3)))
+    s = (torch.empty(npix, dtype=torch.int32, device=rgb.device, pin_memory=rgb.device.type == "cpu")
+         if sel else None)
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    _check(lib().mact_lut_interp_packed(h.ptr, m, _VP(lut4.data_ptr()), n, _VP(rgb.data_ptr()), npix,
+                                        ctypes.byref(ptrs), _VP(s.data_ptr() if s is not None else 0),
+                                        _stream(stream)), "mact_lut_interp_packed")
     return (out, s) if sel else out
 
 

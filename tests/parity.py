@@ -3,6 +3,7 @@
 Tolerances (stated per transform; the kernels compute in FP32, the oracle in
 FP64, both evaluate the same approximant):
   CIELAB  |delta| <= 2e-4 per component (L*, a*, b*)
+  CIELUV  |delta| <= 2e-4 per component (L*, u*, v*), as CIELAB
   HSI     hue: circular |delta| <= 1e-3 degree = 1.745e-5 rad;
           S and I: |delta| <= 1e-6
   SCT     |delta| <= 1e-5 * max(1, |ref|) per component (relative for L,
@@ -36,7 +37,7 @@ def check_space(space, gpu_planes, ref_planes, dtype=torch.float32, what=""):
     """Assert GPU planes (3, ...) match oracle planes (list of 3 arrays)."""
     g = [to_np(gpu_planes[c]).ravel() for c in range(3)]
     r = [np.asarray(ref_planes[c], dtype=np.float64).ravel() for c in range(3)]
-    if space == "cielab":
+    if space in ("cielab", "cieluv"):
         for c in range(3):
             err = np.abs(g[c] - r[c]) - _half_ulp(r[c], dtype)
             k = int(np.argmax(err))
@@ -78,6 +79,8 @@ def oracle_planes(space, rgb_np, exact=False, cfg=None):
     cfg = cfg or {}
     if space == "cielab":
         return O.cielab(rgb_np, exact=exact, n=cfg.get("lab_n", 4), m=cfg.get("lab_m", 4))
+    if space == "cieluv":
+        return O.cieluv(rgb_np, exact=exact, n=cfg.get("lab_n", 4), m=cfg.get("lab_m", 4))
     if space == "hsi":
         return O.hsi(rgb_np, mode="exact" if exact else "approx", n=cfg.get("hsi_n", 5),
                      printed=cfg.get("hsi_coeffs", 0) == 1)

@@ -122,3 +122,34 @@ def test_cached_interp_ragged(h):
         assert np.array_equal(sel.cpu().numpy(), rsel)
         for c in range(3):
             assert np.abs(to_np(out[c]) - ref[c]).max() <= LAB_TOL
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("N", [5, 17, 33, 40])
+def test_packed_lut_equals_unpacked(h, method, N):
+    """mact_lut_pack + mact_lut_interp_packed: the packed nodes are the LUT's
+    values padded with 0, and interpolation from them gives the same
+    selections and the same bits as mact_lut_interp, and the oracle's values,
+    on all 2^24 colours for 17^3 and 33^3 and on a ragged random sample
+    otherwise."""
+    rng = np.random.default_rng(100 + N)
+    lut = oracle_lut(N) if N in (17, 33) else rng.normal(scale=50.0, size=(N, N, N, 3)).astype(np.float32)
+    lt = torch.from_numpy(lut).cuda()
+    lut4 = mact.mact_lut_pack(h, lt)
+    torch.cuda.synchronize()
+    l4 = lut4.cpu().numpy()
+    assert np.array_equal(l4[..., :3], lut) and np.all(l4[..., 3] == 0.0)
+    if N in (17, 33):
+        rgb = torch.from_numpy(np.ascontiguousarray(
+            np.stack(np.meshgrid(np.arange(256), np.arange(256), np.arange(256), indexing="ij"), -1)
+            .reshape(-1, 3).astype(np.uint8))).cuda()
+    else:
+        rgb = torch.from_numpy(rng.integers(0, 256, size=(5003, 3), dtype=np.uint8)).cuda()
+    a, sa = mact.mact_lut_interp_packed(h, method, lut4, rgb, sel=True)
+    b, sb = mact.mact_lut_interp(h, method, lt, rgb, sel=True)
+    torch.cuda.synchronize()
+    assert torch.equal(sa, sb) and torch.equal(a, b)
+    ref, rsel = O.lut_interp(method, lut, rgb.cpu().numpy())
+    assert np.array_equal(sa.cpu().numpy(), rsel)
+    for c in range(3):
+        assert np.abs(to_np(a[c]) - ref[c]).max() <= LAB_TOL

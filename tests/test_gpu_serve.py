@@ -80,14 +80,17 @@ def test_each_result_same_alone_and_in_the_mix(h, mode, mix_requests):
     assert mact.mact_serve_destroy(srv) == 0
 
 
-def test_admission_respects_the_budget(h):
-    """Staged mode, with a budget that holds one 512x512 FP32 request
-    (0.75 + 3 MB) at a time: all requests complete, one after another; a
-    request larger than the whole budget is refused at submit with
-    MACT_E_NOMEM.  In direct mode the same pinned request needs no budget."""
+@pytest.mark.parametrize("mode", ["staged", "direct"])
+def test_admission_respects_the_budget(h, mode):
+    """A budget that holds one 512x512 FP32 request (0.75 + 3 MB of input and
+    output) at a time, in either mode: all requests complete, one per batch,
+    and the admitted bytes never exceed the budget; a request larger than the
+    whole budget is refused at submit with MACT_E_NOMEM.  A server with a
+    larger budget takes it."""
     im = synth.gradient_noise_image(512, 512, seed=1)
-    srv = mact.mact_serve_create(h, 4 << 20, max_slots=8)
-    mact.mact_serve_set_mode(srv, "staged")
+    budget = 4 << 20
+    srv = mact.mact_serve_create(h, budget, max_slots=8)
+    mact.mact_serve_set_mode(srv, mode)
     ref = mact.mact_convert(h, torch.from_numpy(im).cuda(), "cielab").cpu()
     ts = [mact.mact_serve_submit(srv, torch.from_numpy(im).pin_memory(), "cielab") for _ in range(6)]
     for t, out in ts:
@@ -99,7 +102,10 @@ def test_admission_respects_the_budget(h):
     assert e.value.status == -2
     st = mact.mact_serve_stats(srv)
     assert st["completed"] == 6 and st["batches"] == 6
-    mact.mact_serve_set_mode(srv, "direct")
+    assert 0 < st["inflight_bytes_max"] <= budget
+    srv.close()
+    srv = mact.mact_serve_create(h, 64 << 20, max_slots=8)
+    mact.mact_serve_set_mode(srv, mode)
     t, out = mact.mact_serve_submit(srv, big, "cielab")
     mact.mact_serve_wait(srv, t, 30000)
     assert torch.equal(out, mact.mact_convert(h, big.cuda(), "cielab").cpu())
