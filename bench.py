@@ -64,7 +64,7 @@ def peaks():
 
 KERNEL_FILES = {
     "convert": ("common.cuh", "engine.cuh", "pixel.cuh", "convert_common.cuh", "k_convert.cu"),
-    "lut": ("common.cuh", "engine.cuh", "k_lut.cu"),
+    "lut": ("common.cuh", "engine.cuh", "k_lut.cu", "k_lut_interp.cuh", "k_lut_inst.cu"),
 }
 
 
@@ -202,7 +202,7 @@ def run_gpu(args):
             mact.mact_convert(h_exact, rgb, arg, out=out, stream=stream)
         else:
             m, n = arg
-            mact.mact_lut_interp_packed(h_mact, m, luts[n], rgb, out=out.view(3, -1), stream=stream)
+            mact.mact_lut_interp_packed(h_mact, m, luts[n], n, rgb, out=out.view(3, -1), stream=stream)
 
     ev = {name: [] for name, _, _ in ROWS}
 
@@ -473,8 +473,8 @@ def large_headline(steps):
 def run_large_workload(args):
     """Single large images: the 512x512 parity generator (smooth gradients
     over the upper half, uniform noise below) at 8192x8192 and 16384x16384,
-    MACT and exact CIELAB/HSI/SCT, FP32 and FP16 planes; inputs and outputs
-    are far larger than L2."""
+    MACT and exact CIELAB/HSI/SCT and the CIELUV variant, FP32 and FP16
+    planes; inputs and outputs are far larger than L2."""
     import torch
     from paper_1009_0854_gb300 import mact, synth
     dev = torch.device("cuda", 0)
@@ -488,7 +488,7 @@ def run_large_workload(args):
         for dt, dname, bpp in ((torch.float32, "f32", 15), (torch.float16, "f16", 9)):
             out = torch.empty((3, side, side), dtype=dt, device=dev)
             for hname, h in (("mact", hm), ("exact", he), ("mact66", h66)):
-                for space in (("cielab",) if hname == "mact66" else ("cielab", "hsi", "sct")):
+                for space in (("cielab", "cieluv") if hname == "mact66" else ("cielab", "hsi", "sct", "cieluv")):
                     ms = time_convert(torch, mact, h, rgb, space, out, max(5, args.steps // 4))
                     rows["%d_%s_%s_%s" % (side, hname, space, dname)] = {
                         "ms": round(ms, 4), "gpix_s": round(npx / ms / 1e6, 2),
@@ -619,7 +619,7 @@ def run_lut_workload(args):
                     if layout == "standard":
                         fn = lambda v: mact.mact_lut_interp(h, m, lut, v, out=out)
                     elif layout == "packed":
-                        fn = lambda v: mact.mact_lut_interp_packed(h, m, lut4, v, out=out)
+                        fn = lambda v: mact.mact_lut_interp_packed(h, m, lut4, n, v, out=out)
                     else:
                         fn = lambda v: mact.mact_lut_interp_cached(h, m, cache, n, v, out=out)
                     for i in range(3):
@@ -664,6 +664,35 @@ def run_lut_workload(args):
                 "gpix_s": round(PIX / ms / 1e6, 1), "hbm_frac": round(PIX * 15 / (ms * 1e-3) / 1e9 / hbm, 4)}
     print(json.dumps({"workload": "lut: standard vs caching layout, cube and uniform noise, 2^24 px; HSI through "
                       "an angular-hue LUT vs the exact and MACT HSI transforms", "rows": rows}))
+
+
+def run_kernels_workload(args):
+    """One launch of each row of the cube step, then MACT CIELAB with FP16
+    planes, on one copy of the cube, after the LUTs are built and packed:
+    a short, fixed launch sequence for profilers (ncu -k / -c).  Prints the
+    launch order."""
+    import torch
+    from paper_1009_0854_gb300 import mact, synth
+    dev = torch.device("cuda", 0)
+    h, he = mact.mact_create(), mact.mact_create(exact=1)
+    x = torch.from_numpy(synth.rgb_cube()).to(dev)
+    luts = {n: mact.mact_lut_pack(h, mact.mact_lut_build(h, n, device=dev)) for n in (17, 33)}
+    out = torch.empty((3, 4096, 4096), device=dev)
+    o16 = torch.empty((3, 4096, 4096), dtype=torch.float16, device=dev)
+    torch.cuda.synchronize()
+    order = []
+    for name, kind, arg in ROWS:
+        if kind in ("mact", "exact"):
+            mact.mact_convert(h if kind == "mact" else he, x, arg, out=out)
+        else:
+            m, n = arg
+            mact.mact_lut_interp_packed(h, m, luts[n], n, x, out=out.view(3, -1))
+        order.append(name)
+    mact.mact_convert(h, x, "cielab", out=o16)
+    order.append("mact_cielab_f16")
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": "kernels: one launch per row on the 2^24 cube, then MACT CIELAB FP16",
+                      "order": order}))
 
 
 class PinnedRing:
@@ -942,9 +971,11 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=1 << 22)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cube", choices=["cube", "batch", "serve", "grad", "lut", "large"],
+    ap.add_argument("--workload", default="cube",
+                    choices=["cube", "batch", "serve", "grad", "lut", "large", "kernels"],
                     help="cube: the default step; the others measure the batched, served and "
-                         "differentiable forms on their own workloads")
+                         "differentiable forms on their own workloads; kernels: one launch of "
+                         "each row, for profilers")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of --workload serve's trace")
     ap.add_argument("--served-seconds", type=float, default=10.0,
                     help="length of the serving trace in the default line's 'served' key")
@@ -964,6 +995,8 @@ def main():
         run_lut_workload(args)
     elif args.workload == "large":
         run_large_workload(args)
+    elif args.workload == "kernels":
+        run_kernels_workload(args)
     else:
         run_gpu(args)
 

@@ -274,21 +274,26 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
                             const uint8_t *d_rgb, int64_t npix, float *const d_out[3],
                             int32_t *d_sel, mact_stream stream);
 
-/* The same LUT with every node padded to 16 bytes, for repeated
- * interpolation: d_lut4[(((i*n + j)*n + k)*4 + c] = d_lut[((i*n + j)*n + k)*3 + c]
- * for c < 3, and 0 for c = 3.  A LUT with n <= 17 is staged whole in every
- * CTA's shared memory; a larger one (33^3: 575 KB) is read through L1 as
- * 16-byte nodes.  mact_lut_interp repacks such a LUT into handle scratch on
- * every call (and serialises calls on one handle that share that scratch);
- * packing once with mact_lut_pack and calling mact_lut_interp_packed avoids
- * both.  d_lut4 holds n^3 * 4 floats, is owned by the caller and must be
- * 16-byte aligned, else MACT_E_INVAL.  The paper has no counterpart: it is a
+/* The LUT in the layout the interpolation kernels read, for repeated
+ * interpolation: d_packed holds 10 n^3 floats, owned by the caller and
+ * 16-byte aligned (else MACT_E_INVAL):
+ *   floats [0, 4 n^3): node i = ((i_R n + i_G) n + i_B) as (x, y, z, 0);
+ *   floats [4 n^3, 8 n^3): for node i, (x_i, y_i, x_{i+1}, y_{i+1}), the two
+ *     ends of the edge along B that starts there (the last node of a B row
+ *     repeats itself);
+ *   floats [8 n^3, 10 n^3): for node i, (z_i, z_{i+1}).
+ * A LUT with n <= 17 is staged whole in every CTA's shared memory from the
+ * nodes; a larger one (33^3: 575 KB of nodes) is read through L1, trilinear
+ * as 4 edges per pixel instead of 8 nodes.  mact_lut_interp repacks such a
+ * LUT into handle scratch on every call (and orders calls on one handle that
+ * share that scratch); packing once with mact_lut_pack and calling
+ * mact_lut_interp_packed avoids both.  The paper has no counterpart: it is a
  * memory layout of the same LUT. */
-mact_status mact_lut_pack(mact_handle h, const float *d_lut, int32_t n, float *d_lut4, mact_stream stream);
+mact_status mact_lut_pack(mact_handle h, const float *d_lut, int32_t n, float *d_packed, mact_stream stream);
 
-/* mact_lut_interp on a packed LUT (d_lut4 from mact_lut_pack): the same
+/* mact_lut_interp on a packed LUT (d_packed from mact_lut_pack): the same
  * cells, simplices, selection ids and values. */
-mact_status mact_lut_interp_packed(mact_handle h, int32_t method, const float *d_lut4, int32_t n,
+mact_status mact_lut_interp_packed(mact_handle h, int32_t method, const float *d_packed, int32_t n,
                                    const uint8_t *d_rgb, int64_t npix, float *const d_out[3],
                                    int32_t *d_sel, mact_stream stream);
 

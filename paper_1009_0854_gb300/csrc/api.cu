@@ -517,29 +517,30 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
         if (e == cudaSuccess && h->d_lut4) e = cudaFree(h->d_lut4);
         h->d_lut4 = nullptr;
         h->lut4_cap = 0;
-        if (e == cudaSuccess) e = cudaMalloc(&h->d_lut4, nodes * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc(&h->d_lut4, nodes * kLutPackedFloats * sizeof(float));
         if (e != cudaSuccess) return cuda_status(e, "mact_lut_interp: LUT buffer");
         h->lut4_cap = nodes;
     }
     e = cudaStreamWaitEvent(s, h->ev_lut, 0);   // previous reader of the buffer (any stream)
-    if (e == cudaSuccess) e = launch_lut_pack4(d_lut, n, h->d_lut4, s);
-    if (e == cudaSuccess) e = launch_lut_interp(*h, method, nullptr, h->d_lut4, n, d_rgb, npix, d_out, d_sel, s);
+    if (e == cudaSuccess) e = launch_lut_pack(d_lut, n, h->d_lut4, s);
+    if (e == cudaSuccess)
+        e = launch_lut_interp(*h, method, nullptr, reinterpret_cast<const float4 *>(h->d_lut4), n, d_rgb, npix,
+                              d_out, d_sel, s);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_lut, s);
     return cuda_status(e, "mact_lut_interp launch");
 }
 
-mact_status mact_lut_pack(mact_handle h, const float *d_lut, int32_t n, float *d_lut4, mact_stream stream)
+mact_status mact_lut_pack(mact_handle h, const float *d_lut, int32_t n, float *d_packed, mact_stream stream)
 {
     if (!h) return inval("mact_lut_pack: NULL handle");
     if (n < 2 || n > 64) return inval("LUT size must be 2..64");
-    if (!d_lut || !d_lut4) return inval("NULL pointer");
+    if (!d_lut || !d_packed) return inval("NULL pointer");
     if (!aligned4(d_lut)) return inval("d_lut not 4-byte aligned");
-    if ((reinterpret_cast<uintptr_t>(d_lut4) & 15) != 0) return inval("d_lut4 must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(d_packed) & 15) != 0) return inval("d_packed must be 16-byte aligned");
     mact_status st = check_access(*h, d_lut, "d_lut");
-    if (st == MACT_OK) st = check_access(*h, d_lut4, "d_lut4");
+    if (st == MACT_OK) st = check_access(*h, d_packed, "d_packed");
     if (st != MACT_OK) return st;
-    return cuda_status(launch_lut_pack4(d_lut, n, reinterpret_cast<float4 *>(d_lut4), (cudaStream_t)stream),
-                       "mact_lut_pack launch");
+    return cuda_status(launch_lut_pack(d_lut, n, d_packed, (cudaStream_t)stream), "mact_lut_pack launch");
 }
 
 mact_status mact_lut_interp_packed(mact_handle h, int32_t method, const float *d_lut4, int32_t n,
@@ -552,10 +553,10 @@ mact_status mact_lut_interp_packed(mact_handle h, int32_t method, const float *d
     if (npix < 0 || npix > (int64_t(1) << 42)) return inval("pixel count out of range");
     if (npix == 0) return MACT_OK;
     if (!d_lut4 || !d_rgb || !d_out || !d_out[0] || !d_out[1] || !d_out[2]) return inval("NULL pointer");
-    if ((reinterpret_cast<uintptr_t>(d_lut4) & 15) != 0) return inval("d_lut4 must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(d_lut4) & 15) != 0) return inval("d_packed must be 16-byte aligned");
     if (!aligned4(d_out[0]) || !aligned4(d_out[1]) || !aligned4(d_out[2]) || !aligned4(d_sel))
         return inval("d_out[] and d_sel must be 4-byte aligned");
-    mact_status st = check_access(*h, d_lut4, "d_lut4");
+    mact_status st = check_access(*h, d_lut4, "d_packed");
     if (st == MACT_OK) st = check_access(*h, d_rgb, "d_rgb");
     for (int c = 0; c < 3 && st == MACT_OK; ++c) st = check_access(*h, d_out[c], "d_out");
     if (st == MACT_OK) st = check_access(*h, d_sel, "d_sel");

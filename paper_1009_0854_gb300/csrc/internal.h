@@ -48,10 +48,10 @@ struct mact_ctx {
     int batch_next = 0;
     mact::BatchCfg batch_cfg;            // used by mact_convert_batch and new plans
 
-    // LUT interpolation from an unpacked LUT with n > 17: float4 copy,
-    // repacked on every call, grown on demand
+    // LUT interpolation from an unpacked LUT with n > 17: packed copy
+    // (launch_lut_pack), repacked on every call, grown on demand
     std::mutex lut_mu;
-    float4 *d_lut4 = nullptr;
+    float *d_lut4 = nullptr;
     int64_t lut4_cap = 0;                // nodes
     cudaEvent_t ev_lut = nullptr;        // last interpolation kernel that read d_lut4
 
@@ -91,13 +91,17 @@ cudaError_t lut_cached_method(const mact_ctx &h, const float4 *cache, int n, con
 
 // k_lut.cu
 cudaError_t launch_lut_build(const mact_ctx &h, int n, float *d_lut, cudaStream_t s);
-// nodes from d_lut4 (float4) when given, else from d_lut (packed float3);
-// n > 17 needs d_lut4
+// nodes from d_lut4 (the packed layout of launch_lut_pack) when given, else
+// from d_lut (float3); n > 17 needs d_lut4
 cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut, const float4 *d_lut4, int n,
                               const uint8_t *d_rgb, int64_t npix, float *const out[3], int32_t *d_sel,
                               cudaStream_t s);
 bool lut_needs_pack(int n);
 cudaError_t launch_lut_pack4(const float *d_lut, int n, float4 *d_lut4, cudaStream_t s);
+// the packed layout of mact_lut_pack: float4 nodes[n^3], float4 B-edge xy
+// records[n^3], float2 B-edge z records[n^3] (10 n^3 floats)
+constexpr int kLutPackedFloats = 10;
+cudaError_t launch_lut_pack(const float *d_lut, int n, float *d_packed, cudaStream_t s);
 cudaError_t launch_lut_cache_build(const float *d_lut, int n, float4 *d_cache, cudaStream_t s);
 
 // k_lut_hsi.cu: HSI LUT of (cos H, sin H, S, I) nodes, trilinear with the

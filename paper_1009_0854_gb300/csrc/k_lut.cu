@@ -18,9 +18,10 @@
 // LUT placement: for n <= 17 every CTA stages the whole LUT in shared memory
 // as float4 nodes (17^3 x 16 B = 78.6 KB), so a node is one 16-byte shared
 // load.  Larger LUTs (33^3: 575 KB as float4) do not fit and are read as
-// float4 nodes from global memory through L1 (L2 resident): either a copy
-// the caller packed once (mact_lut_pack), or one repacked into handle
-// scratch on every call.  (Staging per 4096-pixel tile only the box of nodes
+// float4 nodes from global memory through L1 (L2 resident), trilinear as
+// 4 B-edge records (xy and z pairs) instead of 8 nodes: either a copy the
+// caller packed once (mact_lut_pack), or one repacked into handle scratch on
+// every call.  (Staging per 4096-pixel tile only the box of nodes
 // the tile touches was measured 3-23% slower on the cube, and 5x slower on
 // noise, where every tile falls back to global memory: not kept.)
 #include <atomic>
@@ -66,6 +67,22 @@ __global__ void k_lut_pack4(const float *__restrict__ lut, int nodes, float4 *__
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nodes) out[i] = make_float4(lut[3 * i], lut[3 * i + 1], lut[3 * i + 2], 0.0f);
+}
+
+// B-edge records of the packed layout, from its float4 nodes: for node i,
+// xy[i] = (x_i, y_i, x_{i+1}, y_{i+1}) and z[i] = (z_i, z_{i+1}) -- the two
+// ends of the edge along B that starts at node i (the record of the last node
+// of a B row repeats it; no cell starts there).  Trilinear interpolation in
+// a LUT too large for shared memory reads its 8 nodes as 4 such edges.
+__global__ void k_lut_edges(const float4 *__restrict__ nodes4, int n, float4 *__restrict__ xy,
+                            float2 *__restrict__ z)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * n * n) return;
+    const float4 a = nodes4[i];
+    const float4 b = (i % n) != n - 1 ? nodes4[i + 1] : a;
+    xy[i] = make_float4(a.x, a.y, b.x, b.y);
+    z[i] = make_float2(a.z, b.z);
 }
 
 // "Caching" layout (the paper's second implementation of each LUT method:
@@ -140,6 +157,16 @@ cudaError_t launch_lut_pack4(const float *d_lut, int n, float4 *d_lut4, cudaStre
 {
     const int nodes = n * n * n;
     k_lut_pack4<<<(nodes + 255) / 256, 256, 0, s>>>(d_lut, nodes, d_lut4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lut_pack(const float *d_lut, int n, float *d_packed, cudaStream_t s)
+{
+    const int nodes = n * n * n;
+    float4 *n4 = reinterpret_cast<float4 *>(d_packed);
+    cudaError_t e = launch_lut_pack4(d_lut, n, n4, s);
+    if (e != cudaSuccess) return e;
+    k_lut_edges<<<(nodes + 255) / 256, 256, 0, s>>>(n4, n, n4 + nodes, reinterpret_cast<float2 *>(n4 + 2 * nodes));
     return cudaGetLastError();
 }
 

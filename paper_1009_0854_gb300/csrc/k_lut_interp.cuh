@@ -305,6 +305,59 @@ k_lut_global(const __grid_constant__ ImageDesc im, const float4 *__restrict__ lu
     run_image<THREADS, float, SEL>(im, ntiles, op, sbuf, sel);
 }
 
+// ------------------------------------- trilinear from B-edge records
+// For LUTs read from global memory, trilinear interpolation fetches its 8
+// nodes as the 4 edges along B of its cell (xy record: the two nodes' x and y,
+// 16 bytes; z record: their z, 8 bytes): 4 + 4 loads of 96 bytes instead of 8
+// loads of 128, which measured 25% faster on the 2^24-colour cube for a 33^3
+// LUT (the kernel is bound by the L1 data path).  Repeated linear
+// interpolation along B, then G, then R, each lerp rounded as
+// fmaf(b - a, w, a); x and y run as packed FP32 pairs.
+template <int N>
+struct OpEdge {
+    const float4 *xy;
+    const float2 *z;
+    int n;
+    __device__ __forceinline__ int operator()(uint32_t r, uint32_t g, uint32_t b, float &o0, float &o1,
+                                              float &o2) const
+    {
+        const int n_ = N > 0 ? N : n;
+        const LocEntry er = loc_entry(r, n_), eg = loc_entry(g, n_), eb = loc_entry(b, n_);
+        const int base = (er.idx * n_ + eg.idx) * n_ + eb.idx;
+        const int sG = n_, sR = n_ * n_;
+        // edges at (R, G) offsets (0, 0), (0, 1), (1, 0), (1, 1)
+        const float4 a0 = __ldg(xy + base), a1 = __ldg(xy + base + sG), a2 = __ldg(xy + base + sR),
+                     a3 = __ldg(xy + base + sR + sG);
+        const float2 z0 = __ldg(z + base), z1 = __ldg(z + base + sG), z2 = __ldg(z + base + sR),
+                     z3 = __ldg(z + base + sR + sG);
+        const float2 wb = make_float2(eb.f, eb.f);
+        const float2 c00 = fma2(sub2(make_float2(a0.z, a0.w), make_float2(a0.x, a0.y)), wb, make_float2(a0.x, a0.y));
+        const float2 c01 = fma2(sub2(make_float2(a1.z, a1.w), make_float2(a1.x, a1.y)), wb, make_float2(a1.x, a1.y));
+        const float2 c10 = fma2(sub2(make_float2(a2.z, a2.w), make_float2(a2.x, a2.y)), wb, make_float2(a2.x, a2.y));
+        const float2 c11 = fma2(sub2(make_float2(a3.z, a3.w), make_float2(a3.x, a3.y)), wb, make_float2(a3.x, a3.y));
+        const float d00 = fmaf(z0.y - z0.x, eb.f, z0.x), d01 = fmaf(z1.y - z1.x, eb.f, z1.x);
+        const float d10 = fmaf(z2.y - z2.x, eb.f, z2.x), d11 = fmaf(z3.y - z3.x, eb.f, z3.x);
+        const float2 wg = make_float2(eg.f, eg.f);
+        const float2 c0 = fma2(sub2(c01, c00), wg, c00), c1 = fma2(sub2(c11, c10), wg, c10);
+        const float d0 = fmaf(d01 - d00, eg.f, d00), d1 = fmaf(d11 - d10, eg.f, d10);
+        const float2 v = fma2(sub2(c1, c0), make_float2(er.f, er.f), c0);
+        o0 = v.x;
+        o1 = v.y;
+        o2 = fmaf(d1 - d0, er.f, d0);
+        return base * 8;   // trilinear: one simplex
+    }
+};
+
+template <int THREADS, int MINB, int N, bool SEL>
+__global__ void __launch_bounds__(THREADS, MINB)
+k_lut_edge(const __grid_constant__ ImageDesc im, const float4 *__restrict__ xy, const float2 *__restrict__ z, int n,
+           int32_t *sel, int64_t ntiles)
+{
+    __shared__ uint4 sbuf[TileShape<THREADS>::vecs];
+    const OpEdge<N> op{xy, z, n};
+    run_image<THREADS, float, SEL>(im, ntiles, op, sbuf, sel);
+}
+
 // ------------------------------------------------------ caching layout
 template <int THREADS, int MINB, int METHOD, int N, bool SEL>
 __global__ void __launch_bounds__(THREADS, MINB)
@@ -436,6 +489,28 @@ static cudaError_t launch_cached(const mact_ctx &h, const float4 *cache, int n, 
     return cudaGetLastError();
 }
 
+// packed: the layout of launch_lut_pack (nodes, then the B-edge records)
+template <int N, bool SEL>
+static cudaError_t launch_edge(const mact_ctx &h, const float4 *packed, int n, const uint8_t *rgb, int64_t npix,
+                               float *const out[3], int32_t *sel, cudaStream_t s)
+{
+    constexpr int T = GlobalShape<MACT_TRILINEAR>::threads;
+    const ImageDesc im = row_desc(rgb, out, npix, TileShape<T>::px);
+    const int64_t nt = im.tiles_per_row;
+    const int64_t nodes = (int64_t)n * n * n;
+    auto kern = k_lut_edge<T, GlobalShape<MACT_TRILINEAR>::ctas, N, SEL>;
+    static std::atomic<int> occ_cache{0};
+    int occ = occ_cache.load(std::memory_order_relaxed);
+    if (occ == 0) {
+        occ = occupancy(kern, T, 0);
+        occ_cache.store(occ, std::memory_order_relaxed);
+    }
+    const int64_t cap = (int64_t)h.num_sms * occ;
+    kern<<<(unsigned)(nt < cap ? nt : cap), T, 0, s>>>(im, packed + nodes, reinterpret_cast<const float2 *>(packed + 2 * nodes),
+                                                        n, sel, nt);
+    return cudaGetLastError();
+}
+
 template <int METHOD, bool SEL>
 cudaError_t lut_interp_method(const mact_ctx &h, const float *lut, const float4 *lut4, int n,
                                  const uint8_t *rgb, int64_t npix, float *const out[3], int32_t *sel, cudaStream_t s)
@@ -443,6 +518,10 @@ cudaError_t lut_interp_method(const mact_ctx &h, const float *lut, const float4 
     if (n == 9) return launch_whole<METHOD, 9, SEL>(h, lut, lut4, n, rgb, npix, out, sel, s);
     if (n == 17) return launch_whole<METHOD, 17, SEL>(h, lut, lut4, n, rgb, npix, out, sel, s);
     if (n <= kLutSmemMaxN) return launch_whole<METHOD, 0, SEL>(h, lut, lut4, n, rgb, npix, out, sel, s);
+    if (METHOD == MACT_TRILINEAR) {
+        if (n == 33) return launch_edge<33, SEL>(h, lut4, n, rgb, npix, out, sel, s);
+        return launch_edge<0, SEL>(h, lut4, n, rgb, npix, out, sel, s);
+    }
     if (n == 33) return launch_global<METHOD, 33, SEL>(h, lut4, n, rgb, npix, out, sel, s);
     return launch_global<METHOD, 0, SEL>(h, lut4, n, rgb, npix, out, sel, s);
 }

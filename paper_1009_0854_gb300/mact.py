@@ -346,30 +346,32 @@ def mact_lut_interp(h, method, lut, rgb, out=None, sel=False, stream=None):
     return (out, s) if sel else out
 
 
+LUT_PACKED_FLOATS = 10   # floats per node of the packed layout (mact_lut_pack)
+
+
 def mact_lut_pack(h, lut, out=None, stream=None):
-    """The (n, n, n, 3) FP32 LUT padded to (n, n, n, 4) float4 nodes, for
-    repeated interpolation with mact_lut_interp_packed."""
+    """The (n, n, n, 3) FP32 LUT in the packed layout the interpolation
+    kernels read (a flat FP32 tensor of 10 n^3 values: the nodes padded to
+    16 bytes, then the B-edge xy and z records), for repeated interpolation
+    with mact_lut_interp_packed."""
     if lut.dtype != torch.float32 or not lut.is_contiguous() or lut.dim() != 4 or lut.shape[3] != 3:
         raise ValueError("lut must be a contiguous (n, n, n, 3) float32 tensor")
     n = lut.shape[0]
     if lut.shape[1] != n or lut.shape[2] != n:
         raise ValueError("lut must be a cube (n, n, n, 3)")
+    size = LUT_PACKED_FLOATS * n ** 3
     if out is None:
-        out = torch.empty((n, n, n, 4), dtype=torch.float32, device=lut.device)
-    _need(out, "out", (n, n, n, 4))
+        out = torch.empty(size, dtype=torch.float32, device=lut.device)
+    _need(out, "out", (size,))
     _check(lib().mact_lut_pack(h.ptr, _VP(lut.data_ptr()), n, _VP(out.data_ptr()), _stream(stream)), "mact_lut_pack")
     return out
 
 
-def mact_lut_interp_packed(h, method, lut4, rgb, out=None, sel=False, stream=None):
-    """mact_lut_interp on a LUT packed by mact_lut_pack ((n, n, n, 4))."""
-    if lut4.dtype != torch.float32 or not lut4.is_contiguous() or lut4.dim() != 4 or lut4.shape[3] != 4:
-        raise ValueError("lut4 must be a contiguous (n, n, n, 4) float32 tensor")
+def mact_lut_interp_packed(h, method, packed, n, rgb, out=None, sel=False, stream=None):
+    """mact_lut_interp on a LUT of size n packed by mact_lut_pack."""
+    _need(packed, "packed", (LUT_PACKED_FLOATS * n ** 3,))
     if rgb.dtype != torch.uint8 or not rgb.is_contiguous() or rgb.shape[-1] != 3:
         raise ValueError("rgb must be a contiguous (..., 3) uint8 tensor")
-    n = lut4.shape[0]
-    if lut4.shape[1] != n or lut4.shape[2] != n:
-        raise ValueError("lut4 must be a cube (n, n, n, 4)")
     npix = rgb.numel() // 3
     if out is None:
         out = torch.empty((3, npix), dtype=torch.float32, device=rgb.device,
@@ -379,7 +381,7 @@ def mact_lut_interp_packed(h, method, lut4, rgb, out=None, sel=False, stream=Non
     s = (torch.empty(npix, dtype=torch.int32, device=rgb.device, pin_memory=rgb.device.type == "cpu")
          if sel else None)
     m = METHODS[method] if isinstance(method, str) else int(method)
-    _check(lib().mact_lut_interp_packed(h.ptr, m, _VP(lut4.data_ptr()), n, _VP(rgb.data_ptr()), npix,
+    _check(lib().mact_lut_interp_packed(h.ptr, m, _VP(packed.data_ptr()), n, _VP(rgb.data_ptr()), npix,
                                         ctypes.byref(ptrs), _VP(s.data_ptr() if s is not None else 0),
                                         _stream(stream)), "mact_lut_interp_packed")
     return (out, s) if sel else out

@@ -217,3 +217,22 @@ def test_full_size_workload_properties(hx):
     g = g.cpu().numpy()
     ok = ~_near_knee(x)[:, None]
     assert np.abs(np.where(ok, g - rg, 0.0)).max() <= 2e-4 * np.abs(rg).max()
+
+
+def test_packed_conversion_kernel_bit_identical_to_scalar_forward():
+    """The conversion kernel evaluates MACT CIELAB with packed FP32x2
+    instructions (the matrix rows X and Y, the d and q Horner chains, a* and
+    b*); the differentiable forward evaluates the same formulas with scalar
+    FMAs in the same order.  Fed the same linear values (each 8-bit code's
+    FP64 inverse gamma rounded to FP32, as both tables hold it), the two give
+    the same bits on every one of the 2^24 colours."""
+    h = mact.mact_create()
+    lin = np.array([O.gamma_inverse(v / 255.0) for v in range(256)], dtype=np.float32)
+    codes = np.arange(1 << 24, dtype=np.int64)
+    rgb = np.stack([(codes >> 16) & 255, (codes >> 8) & 255, codes & 255], axis=1).astype(np.uint8)
+    x = np.ascontiguousarray(lin[rgb.astype(np.int64)].T[None])         # (1, 3, 2^24) linear RGB
+    lab_fwd = mact.mact_lab_forward(h, torch.from_numpy(x).cuda())
+    lab_cnv = mact.mact_convert(h, torch.from_numpy(rgb.reshape(4096, 4096, 3)).cuda(), "cielab")
+    torch.cuda.synchronize()
+    assert torch.equal(lab_fwd.view(3, -1), lab_cnv.view(3, -1))
+    h.close()

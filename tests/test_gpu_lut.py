@@ -128,7 +128,8 @@ def test_cached_interp_ragged(h):
 @pytest.mark.parametrize("N", [5, 17, 33, 40])
 def test_packed_lut_equals_unpacked(h, method, N):
     """mact_lut_pack + mact_lut_interp_packed: the packed nodes are the LUT's
-    values padded with 0, and interpolation from them gives the same
+    values padded with 0, the B-edge records pair each node with the next
+    along B, and interpolation from them gives the same
     selections and the same bits as mact_lut_interp, and the oracle's values,
     on all 2^24 colours for 17^3 and 33^3 and on a ragged random sample
     otherwise."""
@@ -137,15 +138,24 @@ def test_packed_lut_equals_unpacked(h, method, N):
     lt = torch.from_numpy(lut).cuda()
     lut4 = mact.mact_lut_pack(h, lt)
     torch.cuda.synchronize()
-    l4 = lut4.cpu().numpy()
-    assert np.array_equal(l4[..., :3], lut) and np.all(l4[..., 3] == 0.0)
+    p = lut4.cpu().numpy()
+    m = N ** 3
+    nodes = p[:4 * m].reshape(N, N, N, 4)
+    assert np.array_equal(nodes[..., :3], lut) and np.all(nodes[..., 3] == 0.0)
+    # B-edge records: (x_i, y_i, x_{i+1}, y_{i+1}) and (z_i, z_{i+1}); the last
+    # node of a B row repeats itself
+    nxt = np.concatenate([lut[:, :, 1:], lut[:, :, -1:]], axis=2)
+    xy = p[4 * m:8 * m].reshape(N, N, N, 4)
+    z = p[8 * m:].reshape(N, N, N, 2)
+    assert np.array_equal(xy[..., 0:2], lut[..., 0:2]) and np.array_equal(xy[..., 2:4], nxt[..., 0:2])
+    assert np.array_equal(z[..., 0], lut[..., 2]) and np.array_equal(z[..., 1], nxt[..., 2])
     if N in (17, 33):
         rgb = torch.from_numpy(np.ascontiguousarray(
             np.stack(np.meshgrid(np.arange(256), np.arange(256), np.arange(256), indexing="ij"), -1)
             .reshape(-1, 3).astype(np.uint8))).cuda()
     else:
         rgb = torch.from_numpy(rng.integers(0, 256, size=(5003, 3), dtype=np.uint8)).cuda()
-    a, sa = mact.mact_lut_interp_packed(h, method, lut4, rgb, sel=True)
+    a, sa = mact.mact_lut_interp_packed(h, method, lut4, N, rgb, sel=True)
     b, sb = mact.mact_lut_interp(h, method, lt, rgb, sel=True)
     torch.cuda.synchronize()
     assert torch.equal(sa, sb) and torch.equal(a, b)
