@@ -275,20 +275,24 @@ mact_status mact_lut_interp(mact_handle h, int32_t method, const float *d_lut, i
                             int32_t *d_sel, mact_stream stream);
 
 /* The LUT in the layout the interpolation kernels read, for repeated
- * interpolation: d_packed holds 10 n^3 floats, owned by the caller and
- * 16-byte aligned (else MACT_E_INVAL):
- *   floats [0, 4 n^3): node i = ((i_R n + i_G) n + i_B) as (x, y, z, 0);
- *   floats [4 n^3, 8 n^3): for node i, (x_i, y_i, x_{i+1}, y_{i+1}), the two
- *     ends of the edge along B that starts there (the last node of a B row
- *     repeats itself);
- *   floats [8 n^3, 10 n^3): for node i, (z_i, z_{i+1}).
+ * interpolation: d_packed holds 19 n^3 floats, owned by the caller and
+ * 16-byte aligned (else MACT_E_INVAL).  With m = n^3 and node
+ * i = ((i_R n + i_G) n + i_B):
+ *   floats [0, 4m): node i as (x, y, z, 0);
+ *   floats [4m, 8m): B edges, (x_i, y_i, x_j, y_j) with j = i + 1, the next
+ *     node along B (the last node of a B row repeats itself);
+ *   floats [8m, 12m): R edges, the same with j = i + n^2;
+ *   floats [12m, 14m): B edges, (z_i, z_j);  [14m, 16m): R edges, (z_i, z_j);
+ *   floats [16m, 18m): node i as (x, y);  [18m, 19m): node i's z.
  * A LUT with n <= 17 is staged whole in every CTA's shared memory from the
- * nodes; a larger one (33^3: 575 KB of nodes) is read through L1, trilinear
- * as 4 edges per pixel instead of 8 nodes.  mact_lut_interp repacks such a
- * LUT into handle scratch on every call (and orders calls on one handle that
- * share that scratch); packing once with mact_lut_pack and calling
- * mact_lut_interp_packed avoids both.  The paper has no counterpart: it is a
- * memory layout of the same LUT. */
+ * nodes; a larger one (33^3: 575 KB of nodes) is read through L1:
+ * trilinear as 4 B edges, prism as 3 R edges (fewer bytes for the same
+ * loads), the pyramid as single nodes from the xy and z planes, tetrahedral
+ * as 16-byte nodes.
+ * mact_lut_interp repacks such a LUT into handle scratch on every call (and
+ * orders calls on one handle that share that scratch); packing once with
+ * mact_lut_pack and calling mact_lut_interp_packed avoids both.  The paper
+ * has no counterpart: it is a memory layout of the same LUT. */
 mact_status mact_lut_pack(mact_handle h, const float *d_lut, int32_t n, float *d_packed, mact_stream stream);
 
 /* mact_lut_interp on a packed LUT (d_packed from mact_lut_pack): the same

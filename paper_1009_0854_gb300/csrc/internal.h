@@ -98,9 +98,33 @@ cudaError_t launch_lut_interp(const mact_ctx &h, int method, const float *d_lut,
                               cudaStream_t s);
 bool lut_needs_pack(int n);
 cudaError_t launch_lut_pack4(const float *d_lut, int n, float4 *d_lut4, cudaStream_t s);
-// the packed layout of mact_lut_pack: float4 nodes[n^3], float4 B-edge xy
-// records[n^3], float2 B-edge z records[n^3] (10 n^3 floats)
-constexpr int kLutPackedFloats = 10;
+// the packed layout of mact_lut_pack (19 n^3 floats, m = n^3): float4
+// nodes[m], float4 B-edge xy[m], float4 R-edge xy[m], float2 B-edge z[m],
+// float2 R-edge z[m], float2 node xy plane[m], float node z plane[m].  Every
+// array starts at a multiple of its element size times m bytes from a
+// 16-byte aligned base (float4 arrays first, then float2, then float), so
+// each is aligned to its element size for any n.
+constexpr int kLutPackedFloats = 19;
+struct PackedLut {
+    const float4 *nodes;
+    const float4 *bxy, *rxy;
+    const float2 *bz, *rz;
+    const float2 *pxy;
+    const float *pz;
+};
+__host__ __device__ inline PackedLut packed_lut(const float4 *p, int n)
+{
+    const int64_t m = (int64_t)n * n * n;
+    PackedLut k;
+    k.nodes = p;
+    k.bxy = p + m;
+    k.rxy = p + 2 * m;
+    k.bz = reinterpret_cast<const float2 *>(p + 3 * m);
+    k.rz = k.bz + m;
+    k.pxy = k.rz + m;
+    k.pz = reinterpret_cast<const float *>(k.pxy + m);
+    return k;
+}
 cudaError_t launch_lut_pack(const float *d_lut, int n, float *d_packed, cudaStream_t s);
 cudaError_t launch_lut_cache_build(const float *d_lut, int n, float4 *d_cache, cudaStream_t s);
 

@@ -69,20 +69,31 @@ __global__ void k_lut_pack4(const float *__restrict__ lut, int nodes, float4 *__
     if (i < nodes) out[i] = make_float4(lut[3 * i], lut[3 * i + 1], lut[3 * i + 2], 0.0f);
 }
 
-// B-edge records of the packed layout, from its float4 nodes: for node i,
-// xy[i] = (x_i, y_i, x_{i+1}, y_{i+1}) and z[i] = (z_i, z_{i+1}) -- the two
-// ends of the edge along B that starts at node i (the record of the last node
-// of a B row repeats it; no cell starts there).  Trilinear interpolation in
-// a LUT too large for shared memory reads its 8 nodes as 4 such edges.
-__global__ void k_lut_edges(const float4 *__restrict__ nodes4, int n, float4 *__restrict__ xy,
-                            float2 *__restrict__ z)
+// Edge records of the packed layout, from its float4 nodes: for node i and
+// an axis (B: next node i + 1; R: next node i + n^2), xy[i] = (x_i, y_i, x_j,
+// y_j) and z[i] = (z_i, z_j) with j the next node along the axis -- the two
+// ends of the edge that starts at node i (a node at the end of its row along
+// the axis repeats itself; no cell starts there).  In a LUT too large for
+// shared memory, trilinear interpolation reads its 8 nodes as 4 B edges and
+// prism its 6 as 3 R edges; the pyramid reads single nodes from the dense xy
+// (float2) and z (float) planes written here too; tetrahedral reads the
+// 16-byte nodes.
+__global__ void k_lut_edges(const float4 *__restrict__ nodes4, int n, float4 *__restrict__ bxy,
+                            float2 *__restrict__ bz, float4 *__restrict__ rxy, float2 *__restrict__ rz,
+                            float2 *__restrict__ pxy, float *__restrict__ pz)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n * n * n) return;
+    const int nn = n * n;
+    if (i >= nn * n) return;
     const float4 a = nodes4[i];
     const float4 b = (i % n) != n - 1 ? nodes4[i + 1] : a;
-    xy[i] = make_float4(a.x, a.y, b.x, b.y);
-    z[i] = make_float2(a.z, b.z);
+    const float4 r = i / nn != n - 1 ? nodes4[i + nn] : a;
+    bxy[i] = make_float4(a.x, a.y, b.x, b.y);
+    bz[i] = make_float2(a.z, b.z);
+    rxy[i] = make_float4(a.x, a.y, r.x, r.y);
+    rz[i] = make_float2(a.z, r.z);
+    pxy[i] = make_float2(a.x, a.y);
+    pz[i] = a.z;
 }
 
 // "Caching" layout (the paper's second implementation of each LUT method:
@@ -166,7 +177,10 @@ cudaError_t launch_lut_pack(const float *d_lut, int n, float *d_packed, cudaStre
     float4 *n4 = reinterpret_cast<float4 *>(d_packed);
     cudaError_t e = launch_lut_pack4(d_lut, n, n4, s);
     if (e != cudaSuccess) return e;
-    k_lut_edges<<<(nodes + 255) / 256, 256, 0, s>>>(n4, n, n4 + nodes, reinterpret_cast<float2 *>(n4 + 2 * nodes));
+    const PackedLut pk = packed_lut(n4, n);   // the same offsets the kernels read
+    k_lut_edges<<<(nodes + 255) / 256, 256, 0, s>>>(n4, n, const_cast<float4 *>(pk.bxy), const_cast<float2 *>(pk.bz),
+                                                    const_cast<float4 *>(pk.rxy), const_cast<float2 *>(pk.rz),
+                                                    const_cast<float2 *>(pk.pxy), const_cast<float *>(pk.pz));
     return cudaGetLastError();
 }
 

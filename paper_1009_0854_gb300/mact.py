@@ -346,14 +346,15 @@ def mact_lut_interp(h, method, lut, rgb, out=None, sel=False, stream=None):
     return (out, s) if sel else out
 
 
-LUT_PACKED_FLOATS = 10   # floats per node of the packed layout (mact_lut_pack)
+LUT_PACKED_FLOATS = 19   # floats per node of the packed layout (mact_lut_pack)
 
 
 def mact_lut_pack(h, lut, out=None, stream=None):
     """The (n, n, n, 3) FP32 LUT in the packed layout the interpolation
-    kernels read (a flat FP32 tensor of 10 n^3 values: the nodes padded to
-    16 bytes, then the B-edge xy and z records), for repeated interpolation
-    with mact_lut_interp_packed."""
+    kernels read (a flat FP32 tensor of 19 n^3 values: the nodes padded to
+    16 bytes, the B-edge and R-edge xy and z records, and the nodes' dense xy
+    and z planes), for repeated
+    interpolation with mact_lut_interp_packed."""
     if lut.dtype != torch.float32 or not lut.is_contiguous() or lut.dim() != 4 or lut.shape[3] != 3:
         raise ValueError("lut must be a contiguous (n, n, n, 3) float32 tensor")
     n = lut.shape[0]

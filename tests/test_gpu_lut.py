@@ -128,8 +128,8 @@ def test_cached_interp_ragged(h):
 @pytest.mark.parametrize("N", [5, 17, 33, 40])
 def test_packed_lut_equals_unpacked(h, method, N):
     """mact_lut_pack + mact_lut_interp_packed: the packed nodes are the LUT's
-    values padded with 0, the B-edge records pair each node with the next
-    along B, and interpolation from them gives the same
+    values padded with 0, the edge records pair each node with the next
+    along B and along R, and interpolation from them gives the same
     selections and the same bits as mact_lut_interp, and the oracle's values,
     on all 2^24 colours for 17^3 and 33^3 and on a ragged random sample
     otherwise."""
@@ -144,11 +144,15 @@ def test_packed_lut_equals_unpacked(h, method, N):
     assert np.array_equal(nodes[..., :3], lut) and np.all(nodes[..., 3] == 0.0)
     # B-edge records: (x_i, y_i, x_{i+1}, y_{i+1}) and (z_i, z_{i+1}); the last
     # node of a B row repeats itself
-    nxt = np.concatenate([lut[:, :, 1:], lut[:, :, -1:]], axis=2)
-    xy = p[4 * m:8 * m].reshape(N, N, N, 4)
-    z = p[8 * m:].reshape(N, N, N, 2)
-    assert np.array_equal(xy[..., 0:2], lut[..., 0:2]) and np.array_equal(xy[..., 2:4], nxt[..., 0:2])
-    assert np.array_equal(z[..., 0], lut[..., 2]) and np.array_equal(z[..., 1], nxt[..., 2])
+    nb = np.concatenate([lut[:, :, 1:], lut[:, :, -1:]], axis=2)     # next along B
+    nr = np.concatenate([lut[1:], lut[-1:]], axis=0)                 # next along R
+    for xoff, zoff, nxt in ((4 * m, 12 * m, nb), (8 * m, 14 * m, nr)):
+        xy = p[xoff:xoff + 4 * m].reshape(N, N, N, 4)
+        z = p[zoff:zoff + 2 * m].reshape(N, N, N, 2)
+        assert np.array_equal(xy[..., 0:2], lut[..., 0:2]) and np.array_equal(xy[..., 2:4], nxt[..., 0:2])
+        assert np.array_equal(z[..., 0], lut[..., 2]) and np.array_equal(z[..., 1], nxt[..., 2])
+    assert np.array_equal(p[16 * m:18 * m].reshape(N, N, N, 2), lut[..., 0:2])
+    assert np.array_equal(p[18 * m:19 * m].reshape(N, N, N), lut[..., 2])
     if N in (17, 33):
         rgb = torch.from_numpy(np.ascontiguousarray(
             np.stack(np.meshgrid(np.arange(256), np.arange(256), np.arange(256), indexing="ij"), -1)
