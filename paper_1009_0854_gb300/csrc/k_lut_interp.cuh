@@ -38,10 +38,11 @@ __device__ __forceinline__ LocEntry loc_entry(uint32_t v, int n)
 // A node value (three channels) as one FP32 pair and a scalar.  With PK each
 // elementwise step is one packed f32x2 instruction plus one scalar
 // instruction, rounded exactly like three scalar ones; without it, three
-// scalar instructions.  Measured on the 2^24 cube, packing pays only for the
-// tetrahedral method (309 vs 297 Gpix/s at 17^3); for trilinear and prism
-// it was 2-6% slower and it made the pyramid spill (pair registers must be
-// aligned, which raises register pressure).
+// scalar instructions.  Measured on the 2^24 cube, packing pays for the
+// tetrahedral method (309 vs 297 Gpix/s at 17^3) and the 33^3 pyramid
+// (245 vs 238); for trilinear and prism it was 2-6% slower and it made the
+// 17^3 pyramid spill (pair registers must be aligned, which raises register
+// pressure).
 struct V3 {
     float2 xy;
     float z;
@@ -133,7 +134,9 @@ struct Sel {
 template <int METHOD, int SRC, int N, bool RT, bool CACHED = false>
 struct OpLut {
     static constexpr int K = NodeCount<METHOD>::K;
-    static constexpr bool PK = METHOD == MACT_TETRA && !CACHED;   // packed pairs (see V3)
+    // packed pairs (see V3): tetrahedral, and the pyramid read from global
+    // memory (+3% at 33^3; in shared memory its pairs spilled)
+    static constexpr bool PK = (METHOD == MACT_TETRA || (METHOD == MACT_PYRAMID && SRC == kSrcGlobal4)) && !CACHED;
     const float *lut;          // node array (float4 nodes or records, or float3 nodes)
     int n;                     // lattice size (runtime when N == 0)
     Geo<N, RT> geo;
@@ -603,16 +606,16 @@ cudaError_t lut_interp_method(const mact_ctx &h, const float *lut, const float4 
     if (n == 9) return launch_whole<METHOD, 9, SEL>(h, lut, lut4, n, rgb, npix, out, sel, s);
     if (n == 17) return launch_whole<METHOD, 17, SEL>(h, lut, lut4, n, rgb, npix, out, sel, s);
     if (n <= kLutSmemMaxN) return launch_whole<METHOD, 0, SEL>(h, lut, lut4, n, rgb, npix, out, sel, s);
-    if (METHOD == MACT_TRILINEAR) {
+    if constexpr (METHOD == MACT_TRILINEAR) {
         if (n == 33) return launch_edge<33, SEL>(h, lut4, n, rgb, npix, out, sel, s);
         return launch_edge<0, SEL>(h, lut4, n, rgb, npix, out, sel, s);
-    }
-    if (METHOD == MACT_PRISM || METHOD == MACT_PYRAMID) {
+    } else if constexpr (METHOD == MACT_PRISM || METHOD == MACT_PYRAMID) {
         if (n == 33) return launch_packed<METHOD, 33, SEL>(h, lut4, n, rgb, npix, out, sel, s);
         return launch_packed<METHOD, 0, SEL>(h, lut4, n, rgb, npix, out, sel, s);
+    } else {
+        if (n == 33) return launch_global<METHOD, 33, SEL>(h, lut4, n, rgb, npix, out, sel, s);
+        return launch_global<METHOD, 0, SEL>(h, lut4, n, rgb, npix, out, sel, s);
     }
-    if (n == 33) return launch_global<METHOD, 33, SEL>(h, lut4, n, rgb, npix, out, sel, s);
-    return launch_global<METHOD, 0, SEL>(h, lut4, n, rgb, npix, out, sel, s);
 }
 
 template <int METHOD, bool SEL>
