@@ -455,13 +455,15 @@ struct WholeThreads {
 };
 
 
-// Launch shape of the global-memory kernels (about 24 resident warps per SM,
-// 80 registers): trilinear 256 threads x 3 CTAs; the other methods 128 x 6,
-// which measured 2-6% faster for them and 4% slower for trilinear.
+// Launch shape of the global-memory kernels: trilinear 256 threads x 3 CTAs
+// (24 warps per SM, 80 registers); prism 128 x 6 (the same warps, 2-6% faster
+// than 256 x 3 for it); pyramid and tetrahedral 128 x 7 (28 warps at 72
+// registers: +4% over 128 x 6 on the 2^24 cube at 33^3, where the prism lost
+// 2% and spilled).  A 64-register cap (32 warps) spilled and was 2-6% slower.
 template <int METHOD>
 struct GlobalShape {
     static constexpr int threads = METHOD == MACT_TRILINEAR ? 256 : 128;
-    static constexpr int ctas = METHOD == MACT_TRILINEAR ? 3 : 6;
+    static constexpr int ctas = METHOD == MACT_TRILINEAR ? 3 : METHOD == MACT_PRISM ? 6 : 7;
 };
 
 template <class Kern>
