@@ -189,6 +189,9 @@ static mact_status build_coeffs(const mact_config &cfg, Coeffs &co)
         co.lab_rational = 1;
     }
 
+    for (int i = 0; i < 8; ++i) co.lab_dqp[i] = make_float2(co.lab_d[i], co.lab_q[i]);
+    for (int j = 0; j < 3; ++j) co.mp[j] = make_float2(co.m[j], co.m[3 + j]);
+
     // HSI
     if (cfg.hsi_n < 2 || cfg.hsi_n > 5) return inval("hsi_n must be 2..5");
     if (cfg.hsi_coeffs == 0) {

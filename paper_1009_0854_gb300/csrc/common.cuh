@@ -44,6 +44,11 @@ struct Coeffs {
     float luv_c[4];
     double luv_den64[3];
     double luv_u64, luv_v64, luv_un64, luv_vn64;
+    // pairs for the packed FP32 instructions of the FP16-plane kernels, each
+    // one 8-byte operand: (lab_d[i], lab_q[i]) and column j of matrix rows 0
+    // and 1, (m[j], m[3 + j])
+    float2 lab_dqp[8];
+    float2 mp[3];
 };
 
 // One image (or a contiguous run treated as one row) for the tile engine.

@@ -16,8 +16,32 @@ int64_t tiles_of(const ImageDesc &im)
 
 using Shape = TileShape<kThreads>;
 
+// HSI and SCT operators take no table; give them the same aggregate shape.
+template <class Op>
+struct WithTable : Op {
+    __device__ WithTable(const float *, const Coeffs &c) : Op{c} {}
+};
+
+// Minimum resident CTAs per SM each single-image kernel is compiled for (the
+// second __launch_bounds__ argument; 0 = no hint, the compiler's own register
+// budget).  Measured per kernel on the 2^24 cube and a 16384^2 image: a hint
+// of 1 (96-127 registers) makes MACT SCT and CIELUV with FP32 planes 8-9%
+// faster on the large image; 4 (64 registers) makes both HSI forms with FP32
+// planes 1-6% faster on the cube; with FP16 planes MACT CIELAB gains 4% at 4
+// and CIELUV 2% at 3.  The others are fastest with no hint.
+template <class Op, typename OutT>
+struct ImageMinCtas {
+    static constexpr int value = 0;
+};
+template <> struct ImageMinCtas<WithTable<OpSct<false>>, float> { static constexpr int value = 1; };
+template <> struct ImageMinCtas<OpCieluv<false, 4, true>, float> { static constexpr int value = 1; };
+template <> struct ImageMinCtas<WithTable<OpHsi<false>>, float> { static constexpr int value = 4; };
+template <> struct ImageMinCtas<WithTable<OpHsi<true>>, float> { static constexpr int value = 4; };
+template <> struct ImageMinCtas<OpCielab<false, 4, false>, __half> { static constexpr int value = 4; };
+template <> struct ImageMinCtas<OpCieluv<false, 4, false>, __half> { static constexpr int value = 3; };
+
 template <class Op, typename OutT, int TABLE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, ImageMinCtas<Op, OutT>::value)
 k_image(const __grid_constant__ ImageDesc im, const __grid_constant__ Coeffs co,
         const float *__restrict__ gamma, int64_t ntiles)
 {
@@ -27,12 +51,6 @@ k_image(const __grid_constant__ ImageDesc im, const __grid_constant__ Coeffs co,
     const Op op{reinterpret_cast<const float *>(sgam), co};
     run_image<kThreads, OutT, false>(im, ntiles, op, sbuf, nullptr, reinterpret_cast<float *>(sbuf + Shape::vecs));
 }
-
-// HSI and SCT operators take no table; give them the same aggregate shape.
-template <class Op>
-struct WithTable : Op {
-    __device__ WithTable(const float *, const Coeffs &c) : Op{c} {}
-};
 
 template <class Op, typename OutT, int GAMMA>
 static cudaError_t launch_one(const mact_ctx &h, const ImageDesc &im, cudaStream_t s)

@@ -36,10 +36,17 @@ constexpr float kLinOffset = 16.0f / 116.0f;
 template <int DEG, bool NR = true>
 __device__ __forceinline__ float f_mact(float t, const Coeffs &co)
 {
-    float2 s = make_float2(co.lab_d[DEG], co.lab_q[DEG]);
     const float2 tt = make_float2(t, t);
+    float2 s;
+    if constexpr (NR) {
+        s = make_float2(co.lab_d[DEG], co.lab_q[DEG]);
 #pragma unroll
-    for (int i = DEG - 1; i >= 0; --i) s = fma2(s, tt, make_float2(co.lab_d[i], co.lab_q[i]));
+        for (int i = DEG - 1; i >= 0; --i) s = fma2(s, tt, make_float2(co.lab_d[i], co.lab_q[i]));
+    } else {   // FP16 planes: the coefficient pairs stored as pairs
+        s = co.lab_dqp[DEG];
+#pragma unroll
+        for (int i = DEG - 1; i >= 0; --i) s = fma2(s, tt, co.lab_dqp[i]);
+    }
     float fa = fmaf(s.x, NR ? rcp_nr(s.y) : rcp_approx(s.y), 1.0f);
     float fl = fmaf(kLinSlope, t, kLinOffset);
     return t > kKnee ? fa : fl;
@@ -86,6 +93,20 @@ __device__ __forceinline__ float f_exact(float t)
     return t > kKnee ? cbrtf(t) : fl;
 }
 
+// Rows 0 and 1 of the white-divided matrix times the linearised code as one
+// FP32 pair; NR = false (FP16 planes) takes each coefficient pair as one
+// stored 8-byte operand.
+template <bool NR>
+__device__ __forceinline__ float2 rows01(const Coeffs &co, float k0, float k1, float k2)
+{
+    if constexpr (NR)
+        return fma2(make_float2(co.m[2], co.m[5]), make_float2(k2, k2),
+                    fma2(make_float2(co.m[1], co.m[4]), make_float2(k1, k1),
+                         mul2(make_float2(co.m[0], co.m[3]), make_float2(k0, k0))));
+    else
+        return fma2(co.mp[2], make_float2(k2, k2), fma2(co.mp[1], make_float2(k1, k1), mul2(co.mp[0], make_float2(k0, k0))));
+}
+
 // RDEG: 0 = the FP64 cube-root polynomial; 4 or 6 = the rational with
 // chains of that degree (ignored when EXACT).  NR: Newton step on the
 // rational's reciprocal (off for FP16 planes).  The X and Y rows of the
@@ -93,8 +114,11 @@ __device__ __forceinline__ float f_exact(float t)
 // rational: for FP32 planes each channel's (d, q) chains (66 instructions
 // per pixel, 75 registers; the kernel is HBM-bound there, and this form
 // measured 3% faster on a 16384^2 image), for FP16 planes the X and Y
-// channels together (f_mact_xy: 56 instructions per pixel; issue-bound).
-// All forms are bit-identical to the scalar ones.
+// channels together (f_mact_xy), with the matrix and Z-chain coefficient
+// pairs read as stored 8-byte pairs (52 instructions per pixel; issue-bound).
+// Stored pairs for FP32 planes cut them to 60 instructions per pixel but
+// measured 2-4% slower on a 16384^2 image.  All forms are bit-identical to
+// the scalar ones.
 template <bool EXACT, int RDEG, bool NR = true>
 struct OpCielab {
     const float *gam;   // 256-entry linearisation table in shared memory
@@ -116,9 +140,7 @@ struct OpCielab {
         }
         float k0 = gam[r], k1 = gam[g], k2 = gam[b];
         // (tx, ty) = rows 0 and 1 of the matrix, tz = row 2
-        const float2 txy = fma2(make_float2(co.m[2], co.m[5]), make_float2(k2, k2),
-                                fma2(make_float2(co.m[1], co.m[4]), make_float2(k1, k1),
-                                     mul2(make_float2(co.m[0], co.m[3]), make_float2(k0, k0))));
+        const float2 txy = rows01<NR>(co, k0, k1, k2);
         float tz = fmaf(co.m[8], k2, fmaf(co.m[7], k1, co.m[6] * k0));
         float fx, fy, fz;
         if (EXACT) {
@@ -176,9 +198,7 @@ struct OpCieluv {
             return 0;
         }
         float k0 = gam[r], k1 = gam[g], k2 = gam[b];
-        const float2 txy = fma2(make_float2(co.m[2], co.m[5]), make_float2(k2, k2),
-                                fma2(make_float2(co.m[1], co.m[4]), make_float2(k1, k1),
-                                     mul2(make_float2(co.m[0], co.m[3]), make_float2(k0, k0))));
+        const float2 txy = rows01<NR>(co, k0, k1, k2);
         float tz = fmaf(co.m[8], k2, fmaf(co.m[7], k1, co.m[6] * k0));
         float fy;
         if (EXACT) {
