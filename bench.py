@@ -85,10 +85,11 @@ def source_hash(group):
     return h.hexdigest()[:12]
 
 
-def traffic_table():
-    """Per-launch DRAM bytes (read + write) from the committed ncu summary
-    profiles/traffic.txt, for rows whose kernel sources still hash the same."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
+def profile_table(fname):
+    """Per-row figures from a committed ncu summary under profiles/ (lines
+    "row value source_hash"), for rows whose kernel sources still hash the
+    same as when the figure was taken."""
+    path = os.path.join(ROOT, "profiles", fname)
     out = {}
     if not os.path.exists(path):
         return out
@@ -98,6 +99,34 @@ def traffic_table():
         if len(line) == 3 and line[2] == cur[kernel_group(line[0])]:
             out[line[0]] = float(line[1])
     return out
+
+
+def traffic_table():
+    """Per-launch DRAM bytes (read + write) from profiles/traffic.txt."""
+    return profile_table("traffic.txt")
+
+
+def instruction_table():
+    """Instructions per pixel (warp instructions x 32 / pixels) from
+    profiles/instructions.txt."""
+    return profile_table("instructions.txt")
+
+
+# Rows bound by instruction issue rather than by memory: the exact SCT runs two
+# atan2f and two IEEE sqrtf per pixel.  Their roofline is the issue rate.
+ALU_ROWS = ("exact_sct",)
+
+
+def issue_peak(num_sms):
+    """Lane-instructions per second at full issue, in T/s: SMs x 4 schedulers
+    x one warp instruction per cycle x 32 lanes x the maximum SM clock (from
+    MEASURED_PEAKS.json, else the GB300's 2070 MHz)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mhz, kind = float(json.load(fh)["sm_max_mhz"]), "measured sm_max_mhz"
+    except Exception:  # noqa: BLE001 - the part's maximum clock
+        mhz, kind = 2070.0, "nominal 2070 MHz"
+    return num_sms * 4 * 32 * mhz * 1e6 / 1e12, "%d SMs x 4 issue x 32 lanes x %s" % (num_sms, kind)
 
 
 class ClockSampler:
@@ -245,12 +274,20 @@ def run_gpu(args):
     row_ms = {name: statistics.mean(a.elapsed_time(b) for a, b in ev[name]) for name in ev}
     hbm, peak_kind = peaks()
     traffic = traffic_table()
+    insts = instruction_table()
+    ipeak, ipeak_kind = issue_peak(torch.cuda.get_device_properties(dev).multi_processor_count)
     bytes_px = 3 + 12
 
     def roof(name):
         t = row_ms[name] * 1e-3
-        achieved = PIX * bytes_px / t / 1e9
         tr = traffic.get(name)
+        if name in ALU_ROWS and name in insts:
+            achieved = insts[name] * PIX / t / 1e12
+            return {"bound": "alu", "achieved": round(achieved, 2), "peak": round(ipeak, 2), "unit": "Tinst/s",
+                    "frac": round(achieved / ipeak, 4), "traffic": tr, "kernel": name,
+                    "peak_source": ipeak_kind, "inst_per_px": insts[name],
+                    "ms_per_launch": round(row_ms[name], 5)}
+        achieved = PIX * bytes_px / t / 1e9
         return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "traffic": tr, "kernel": name,
                 "peak_source": peak_kind, "ms_per_launch": round(row_ms[name], 5)}

@@ -121,9 +121,30 @@ def test_traffic_figures_only_for_unchanged_kernel_sources(tmp_path, monkeypatch
 
 
 def test_committed_traffic_rows_name_known_kernel_groups():
-    rows = [l.split("#", 1)[0].split() for l in open(bench.os.path.join(bench.ROOT, "profiles", "traffic.txt"))]
-    rows = [r for r in rows if r]
-    assert rows and all(len(r) == 3 and bench.kernel_group(r[0]) in bench.KERNEL_FILES for r in rows)
+    for fname in ("traffic.txt", "instructions.txt"):
+        rows = [l.split("#", 1)[0].split() for l in open(bench.os.path.join(bench.ROOT, "profiles", fname))]
+        rows = [r for r in rows if r]
+        assert rows and all(len(r) == 3 and bench.kernel_group(r[0]) in bench.KERNEL_FILES for r in rows)
+        assert all(r[0] in {name for name, _, _ in bench.ROWS} for r in rows)
+
+
+def test_instruction_figures_only_for_unchanged_kernel_sources(tmp_path, monkeypatch):
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "instructions.txt").write_text("exact_sct 150.5 aaaa\nlut17_tetra 90.4 bbbb\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "source_hash", lambda g: {"convert": "aaaa", "lut": "cccc"}[g])
+    assert bench.instruction_table() == {"exact_sct": 150.5}
+
+
+def test_issue_peak_is_lanes_times_schedulers_times_clock(tmp_path, monkeypatch):
+    """The ALU roofline's peak: 152 SMs x 4 schedulers x 32 lanes x 2070 MHz
+    = 40.29 T lane-instructions per second."""
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))   # no MEASURED_PEAKS.json: the nominal clock
+    peak, kind = bench.issue_peak(152)
+    assert abs(peak - 152 * 4 * 32 * 2070e6 / 1e12) < 1e-9 and "2070" in kind
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6700.0, "sm_max_mhz": 1965.0}')
+    peak, kind = bench.issue_peak(152)
+    assert abs(peak - 152 * 128 * 1965e6 / 1e12) < 1e-9 and "measured" in kind
 
 
 def test_reference_arm_prints_the_contract_line():
