@@ -426,7 +426,7 @@ mact_status mact_convert_batch(mact_handle h, const mact_image *imgs, int32_t co
             total += tiles_of(d);
             list.img[n++] = d;
         }
-        int per_sm = batch_blocks_per_sm(*h, cfg);
+        int per_sm = batch_blocks_per_sm(*h, cfg, true);
         if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
         int64_t grid = (int64_t)h->num_sms * per_sm;
         if (grid > total) grid = total;

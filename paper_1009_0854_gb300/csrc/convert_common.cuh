@@ -30,11 +30,11 @@ __device__ __forceinline__ void load_table(int kind, const float *gamma, double 
 
 // Batched kernels of one cube-root form (EXACT: libm; else RDEG 4 or 6: the
 // rational's degree, 0: the FP64 polynomial) and one launch shape (T threads,
-// S sub-blocks): resident CTAs per SM, and launches from a device work list
-// or a by-value list.  Each (form, shape) pair is instantiated in its own
-// object (k_batch_inst.cu).
+// S sub-blocks): resident CTAs per SM of the device-list or (param) the
+// by-value kernel, and launches from a device work list or a by-value list.
+// Each (form, shape) pair is instantiated in its own object (k_batch_inst.cu).
 template <bool EXACT, int RDEG, int T, int S>
-int batch_occ_shape();
+int batch_occ_shape(bool param);
 template <bool EXACT, int RDEG, int T, int S>
 cudaError_t batch_launch_shape(const mact_ctx &h, const ImageDesc *d_imgs, int32_t count, int64_t total,
                                unsigned long long *d_ctr, int grid, cudaStream_t s);
@@ -44,9 +44,9 @@ cudaError_t batch_launch_param_shape(const mact_ctx &h, const ParamList &list, i
 
 // The same for a form, dispatched on the shape.
 template <bool EXACT, int RDEG>
-int batch_occ(const BatchCfg &cfg)
+int batch_occ(const BatchCfg &cfg, bool param)
 {
-#define MACT_OCC(T, S) if (cfg.threads == T && cfg.subs == S) return batch_occ_shape<EXACT, RDEG, T, S>();
+#define MACT_OCC(T, S) if (cfg.threads == T && cfg.subs == S) return batch_occ_shape<EXACT, RDEG, T, S>(param);
     MACT_BATCH_SHAPES(MACT_OCC)
 #undef MACT_OCC
     return 1;

@@ -75,7 +75,8 @@ cudaError_t launch_batch(const mact_ctx &h, const ImageDesc *d_imgs, int32_t cou
 // kernel parameters (no device list, no counters)
 cudaError_t launch_batch_param(const mact_ctx &h, const ParamList &list, int32_t count, int64_t total_tiles,
                                int grid, cudaStream_t s, const BatchCfg &cfg);
-int batch_blocks_per_sm(const mact_ctx &h, const BatchCfg &cfg = BatchCfg());
+// resident CTAs per SM of the device-list kernel, or (param) of the by-value one
+int batch_blocks_per_sm(const mact_ctx &h, const BatchCfg &cfg = BatchCfg(), bool param = false);
 bool batch_cfg_supported(const BatchCfg &cfg);
 
 constexpr int kLutSmemMaxN = 17;   // largest LUT staged whole in every CTA's shared memory

@@ -108,19 +108,23 @@ k_batch_param(const __grid_constant__ ParamList list, int32_t count, int64_t tot
 }
 
 // Per-shape entry points (declared in convert_common.cuh): resident CTAs per
-// SM, and launches from a device work list or a by-value list.
+// SM of the device-list kernel or (param) of the by-value kernel, and
+// launches of either.  Each form is sized by its own figure: the by-value
+// kernel holds its list in the parameter block and can need more registers,
+// which must not shrink the device-list kernel's grid.
 template <bool EXACT, int RDEG, int T, int S>
-int batch_occ_shape()
+int batch_occ_shape(bool param)
 {
-    static const int occ = [] {   // thread-safe one-time init
+    struct Occ {
+        int list, param;
+    };
+    static const Occ occ = [] {   // thread-safe one-time init
         int o = 0, op = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch<EXACT, RDEG, T, S>, T, 0);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_batch_param<EXACT, RDEG, T, S>, T, 0);
-        if (op < o) o = op;   // one figure serves both forms
-        return (e != cudaSuccess || o <= 0) ? 1 : o;
+        cudaError_t ep = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_batch_param<EXACT, RDEG, T, S>, T, 0);
+        return Occ{(e != cudaSuccess || o <= 0) ? 1 : o, (ep != cudaSuccess || op <= 0) ? 1 : op};
     }();
-    return occ;
+    return param ? occ.param : occ.list;
 }
 
 template <bool EXACT, int RDEG, int T, int S>
@@ -144,7 +148,7 @@ cudaError_t batch_launch_param_shape(const mact_ctx &h, const ParamList &list, i
 // Explicit instantiation of one (form, shape) pair's entry points (inside
 // namespace mact).
 #define MACT_BATCH_SHAPE(EXACT, RDEG, T, S)                                                                  \
-    template int batch_occ_shape<EXACT, RDEG, T, S>();                                                        \
+    template int batch_occ_shape<EXACT, RDEG, T, S>(bool);                                                    \
     template cudaError_t batch_launch_shape<EXACT, RDEG, T, S>(const mact_ctx &, const ImageDesc *, int32_t,  \
                                                                int64_t, unsigned long long *, int, cudaStream_t); \
     template cudaError_t batch_launch_param_shape<EXACT, RDEG, T, S>(const mact_ctx &, const ParamList &,     \

@@ -111,11 +111,11 @@ bool batch_cfg_supported(const BatchCfg &cfg)
     return false;
 }
 
-int batch_blocks_per_sm(const mact_ctx &h, const BatchCfg &cfg)
+int batch_blocks_per_sm(const mact_ctx &h, const BatchCfg &cfg, bool param)
 {
-    if (h.cfg.exact) return batch_occ<true, 4>(cfg);
-    if (!h.co.lab_rational) return batch_occ<false, 0>(cfg);
-    return h.co.lab_deg == 6 ? batch_occ<false, 6>(cfg) : batch_occ<false, 4>(cfg);
+    if (h.cfg.exact) return batch_occ<true, 4>(cfg, param);
+    if (!h.co.lab_rational) return batch_occ<false, 0>(cfg, param);
+    return h.co.lab_deg == 6 ? batch_occ<false, 6>(cfg, param) : batch_occ<false, 4>(cfg, param);
 }
 
 cudaError_t launch_batch_param(const mact_ctx &h, const ParamList &list, int32_t count, int64_t total, int grid,

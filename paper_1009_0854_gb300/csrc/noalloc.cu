@@ -118,8 +118,11 @@ extern "C" mact_status mact_convert_batch_static(mact_handle h, const mact_image
         std::lock_guard<std::mutex> lock(h->batch_mu);
         cfg = h->batch_cfg;
     }
-    int per_sm = batch_blocks_per_sm(*h, cfg);
-    if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
+    // resident CTAs per SM of the kernel form that runs: by value or from the list
+    auto per_sm_of = [&](bool param) {
+        int per_sm = batch_blocks_per_sm(*h, cfg, param);
+        return (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) ? cfg.ctas_per_sm : per_sm;
+    };
 
     int32_t nonempty = 0;
     for (int32_t i = 0; i < count; ++i) nonempty += (imgs[i].width != 0 && imgs[i].height != 0);
@@ -135,7 +138,7 @@ extern "C" mact_status mact_convert_batch_static(mact_handle h, const mact_image
             total += tiles_of(d);
             list.img[n++] = d;
         }
-        int64_t grid = (int64_t)h->num_sms * per_sm;
+        int64_t grid = (int64_t)h->num_sms * per_sm_of(true);
         if (grid > total) grid = total;
         return cuda_status(launch_batch_param(*h, list, n, total, (int)grid, s, cfg),
                            "mact_convert_batch_static launch");
@@ -165,7 +168,7 @@ extern "C" mact_status mact_convert_batch_static(mact_handle h, const mact_image
             fill = 0;
         }
     }
-    int64_t grid = (int64_t)h->num_sms * per_sm;
+    int64_t grid = (int64_t)h->num_sms * per_sm_of(false);
     if (grid > total) grid = total;
     return cuda_status(launch_batch(*h, d_imgs, n, total, d_ctr, (int)grid, s, cfg),
                        "mact_convert_batch_static launch");
