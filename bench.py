@@ -835,7 +835,7 @@ def serve_experiment(seconds, paths=("direct", "staged", "direct_fitted66", "pla
     h66 = mact.mact_create(lab_coeffs=1, lab_n=6, lab_m=6)
 
     def served(tr, mode, hs=None):
-        """The driver submits at each arrival time and, while waiting for the
+        """The load generator submits at each arrival time and, while waiting for the
         next one, retires every finished request (its ring slot is released)."""
         srv = mact.mact_serve_create(hs or h, budget, max_slots=128)
         mact.mact_serve_set_mode(srv, mode)
